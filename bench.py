@@ -1,0 +1,390 @@
+"""Benchmark: grid nodes/s of the full hot path on the synthetic survey swath.
+
+One step = one pass of the whole path over the swath held in HBM:
+    upload + validate + spatial-hash build (bg_soundings_upload, device input)
+    -> IDW k=16, p=2 over every grid node      (bg_interp_idw)
+    -> ordinary kriging k=32, spherical        (bg_interp_okrige)
+Workload: 4 survey lines x 20,000 pings x 256 beams = 20.48M soundings, grid
+20,000 x 3,692 nodes at 0.5 m (73.84M nodes); every node gets an IDW depth, a
+kriging depth and a kriging variance. value = grid nodes / s of the step.
+
+The inputs (246 MB of soundings) and outputs (886 MB) exceed the 129 MB L2,
+so consecutive steps do not run from cache.
+
+`--impl reference` times the FP64 CPU oracle on a bounded sample of nodes of
+the same workload on the host cores (the only other program of this path).
+Under torchrun every rank grids its own copy of the swath (weak scaling, no
+collective); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "grid nodes/s (IDW k=16, kriging k=32)"
+IDW_K, IDW_P = 16, 2.0
+OK_K = 32
+VGM = (0, 0.25, 100.0, 50.0)  # spherical, nugget 0.25 m^2, total sill 100 m^2, range 50 m
+
+# Algorithmic work per node of the kriging kernel at k = 32 (reduced system of
+# n = 31 unknowns), FP32 flops (an FMA counts 2): Cholesky n^3/3, two solves
+# (solution + refinement correction) of 2 n^2 each, assembly of n(n+1)/2
+# variogram entries at ~12 flops (dx^2+dy^2, sqrt, scale, cubic) plus the
+# n^2 matrix fill (2 flops). The FP64 residual (n^2 FMA) is counted apart.
+def okrige_flops_per_node(k=OK_K):
+    n = k - 1
+    chol = n ** 3 / 3.0
+    solves = 2 * (2 * n * n)
+    assembly = 12 * (n * (n + 1) / 2 + n) + 2 * n * n
+    return chol + solves + assembly
+
+
+def okrige_fp64_flops_per_node(k=OK_K):
+    n = k - 1
+    return 2 * n * n
+
+
+# FP32 peak for "alu"-bound roofline: 152 SMs x 128 FP32 lanes x 2 flops/FMA x
+# the maximum SM clock (2,070 MHz) = 80.5 TFLOP/s.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+# ------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.dev)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [v.strip() for v in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# -------------------------------------------------------------- CPU oracle
+
+def oracle_sample(w, nodes: int, seed: int = 0):
+    g = w.grid
+    rng = np.random.default_rng(seed)
+    sel = rng.choice(g.m, nodes, replace=False)
+    qx = (g.x0_cm + (sel % g.nx) * g.cell_cm + g.cell_cm // 2).astype(np.int32)
+    qy = (g.y0_cm + (sel // g.nx) * g.cell_cm + g.cell_cm // 2).astype(np.int32)
+    return qx, qy
+
+
+def run_oracle(w, qx, qy):
+    import oracle
+    oracle.idw(w.x_cm, w.y_cm, w.z_m, qx, qy, IDW_K, IDW_P)
+    oracle.okrige(w.x_cm, w.y_cm, w.z_m, qx, qy, OK_K, *VGM)
+
+
+def cpu_baseline(w, target_s: float = 15.0):
+    """Time the FP64 oracle on a bounded sample of nodes (~target_s of CPU work)."""
+    import oracle
+    cores = oracle.threads()
+    qx, qy = oracle_sample(w, max(cores, 8), seed=99)
+    t0 = time.perf_counter()
+    run_oracle(w, qx, qy)
+    per_node = (time.perf_counter() - t0) / qx.size
+    n = int(max(cores, min(200_000, target_s / max(per_node, 1e-9))))
+    qx, qy = oracle_sample(w, n, seed=7)
+    t0 = time.perf_counter()
+    run_oracle(w, qx, qy)
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": "nodes/s", "cores": cores, "kind": "oracle",
+            "sample": f"{n} random nodes of the {w.grid.nx}x{w.grid.ny} swath grid, brute-force "
+                      f"exact k-NN over all {w.x_cm.size} soundings, FP64 IDW k={IDW_K} + "
+                      f"kriging k={OK_K} per node ({dt:.1f} s)"}
+
+
+# ------------------------------------------------------------------- main
+
+def workload(args):
+    if args.small:
+        return synth.swath(seed=2, lines=2, pings=2000, beams=256)
+    return synth.swath(seed=2)
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def bench_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    w = workload(args)
+    import oracle
+    cores = oracle.threads()
+    per_step_nodes = max(cores, int(args.ref_nodes))
+    for i in range(args.warmup):
+        qx, qy = oracle_sample(w, min(per_step_nodes, cores), seed=1000 + i)
+        run_oracle(w, qx, qy)
+    times = []
+    for i in range(args.steps):
+        qx, qy = oracle_sample(w, per_step_nodes, seed=i)
+        t0 = time.perf_counter()
+        run_oracle(w, qx, qy)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = per_step_nodes * args.steps / total
+    sample = (f"{per_step_nodes} random nodes per step of the {w.grid.nx}x{w.grid.ny} swath grid; "
+              f"brute-force exact k-NN over {w.x_cm.size} soundings, FP64 IDW k={IDW_K} + kriging "
+              f"k={OK_K}")
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "nodes/s",
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": config_dict(w, args),
+           "cpu_baseline": {"value": value, "unit": "nodes/s", "cores": cores, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": value, "unit": "nodes/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def config_dict(w, args):
+    g = w.grid
+    return {"workload": ("survey swath, 4 lines x 20,000 pings x 256 beams (20.48M soundings), "
+                         "grid 20,000 x 3,692 at 0.5 m" if not args.small else
+                         "survey swath, 2 lines x 2,000 pings x 256 beams, grid at 0.5 m"),
+            "soundings": int(w.x_cm.size), "nodes": int(g.m), "grid": [g.nx, g.ny, g.cell_cm],
+            "idw": {"k": IDW_K, "power": IDW_P},
+            "kriging": {"k": OK_K, "model": "spherical", "nugget_m2": VGM[1], "sill_m2": VGM[2],
+                        "range_m": VGM[3]},
+            "seed": w.params["seed"], "l2": "inputs and outputs larger than L2 (no flush)",
+            "parallelism": f"replica x{args.gpus}"}
+
+
+def bench_ours(args):
+    import torch
+
+    import paper_2505_22675_gb300 as bg
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = workload(args)
+    g = w.grid
+    m = g.m
+    ctx = bg.ctx_create(local)
+    grid = bg.grid_create(ctx, g.x0_cm, g.y0_cm, g.cell_cm, g.nx, g.ny)
+    xd, yd, zd = (torch.from_numpy(a).to(dev) for a in (w.x_cm, w.y_cm, w.z_m))
+    d_idw = torch.empty(m, device=dev)
+    d_ok = torch.empty(m, device=dev)
+    v_ok = torch.empty(m, device=dev)
+    vgm = bg.variogram(*VGM)
+    stream = torch.cuda.current_stream(dev)
+
+    ev = {k: [] for k in ("hash", "idw", "ok")}
+
+    def step(record):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e2 = torch.cuda.Event(enable_timing=True)
+        e3 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s = bg.soundings_upload(ctx, xd, yd, zd)
+        e1.record(stream)
+        bg.interp_idw(s, grid, IDW_K, IDW_P, d_idw)
+        e2.record(stream)
+        bg.interp_okrige(s, grid, OK_K, vgm, d_ok, v_ok)
+        e3.record(stream)
+        bg.soundings_destroy(s)
+        if record:
+            ev["hash"].append((e0, e1))
+            ev["idw"].append((e1, e2))
+            ev["ok"].append((e2, e3))
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        step(False)
+    torch.cuda.synchronize()
+    barrier()
+    launches0 = bg.launch_count()
+    start = torch.cuda.Event(enable_timing=True)
+    stop = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        start.record(stream)
+        for _ in range(args.steps):
+            step(True)
+        stop.record(stream)
+        torch.cuda.synchronize()
+    launches = bg.launch_count() - launches0
+    barrier()
+    ms = start.elapsed_time(stop) / args.steps
+    stage = {k: statistics.median(a.elapsed_time(b) for a, b in v) for k, v in ev.items()}
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ws * m / (ms / 1e3)
+
+    # ---- end to end through the C ABI with host buffers (pinned), copies timed
+    xh, yh, zh = (torch.from_numpy(a).pin_memory() for a in (w.x_cm, w.y_cm, w.z_m))
+    out_h = [torch.empty(m, pin_memory=True) for _ in range(3)]
+
+    def e2e_step():
+        s = bg.soundings_upload(ctx, xh, yh, zh, stream=stream)
+        bg.interp_idw(s, grid, IDW_K, IDW_P, d_idw)
+        bg.interp_okrige(s, grid, OK_K, vgm, d_ok, v_ok)
+        for h, d in zip(out_h, (d_idw, d_ok, v_ok)):
+            h.copy_(d, non_blocking=True)
+        bg.soundings_destroy(s)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    barrier()
+    e_steps = max(1, min(args.steps, 3))
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(e_steps):
+        e2e_step()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = t0.elapsed_time(t1) / e_steps
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    bad = int(torch.isnan(d_idw).sum() + torch.isnan(d_ok).sum())
+
+    if rank == 0:
+        peaks = load_peaks()
+        flops = okrige_flops_per_node() * m
+        ok_s = stage["ok"] / 1e3
+        achieved = flops / ok_s / 1e12
+        clocks = clk.summary()
+        out = {
+            "metric": METRIC, "value": value, "unit": "nodes/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": config_dict(w, args),
+            "stages_ms": {"hash_build": stage["hash"], "idw_k16": stage["idw"],
+                          "kriging_k32": stage["ok"]},
+            "idw_nodes_per_s": m / (stage["idw"] / 1e3),
+            "kriging_nodes_per_s": m / ok_s,
+            "roofline": {"bound": "alu", "kernel": "k_okrige<32> (kNN + kriging k=32)",
+                         "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                         "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
+                         "flops_per_node": okrige_flops_per_node(),
+                         "fp64_flops_per_node": okrige_fp64_flops_per_node(),
+                         "hbm_peak_gbs_measured": peaks.get("hbm_gbs")},
+            "e2e": {"value": ws * m / (e2e_ms / 1e3), "unit": "nodes/s",
+                    "h2d_bytes_per_step": int(12 * w.x_cm.size),
+                    "d2h_bytes_per_step": int(12 * m), "ms_per_step": e2e_ms},
+            "gpu_launches": int(launches), "clocks": clocks, "nan_outputs": bad,
+        }
+        if not args.no_cpu_baseline and ws == 1:
+            out["cpu_baseline"] = cpu_baseline(w, target_s=args.cpu_seconds)
+        print(json.dumps(out), flush=True)
+    bg.grid_destroy(grid)
+    bg.ctx_destroy(ctx)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--small", action="store_true", help="2-line swath (quick check / profiling)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-nodes", type=int, default=256, help="reference arm: nodes per step")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        bench_reference(args)
+    else:
+        bench_ours(args)
+
+
+if __name__ == "__main__":
+    main()

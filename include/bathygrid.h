@@ -1,0 +1,169 @@
+/*
+ * bathygrid — gridding scattered multibeam soundings on one GB300 GPU.
+ *
+ * C ABI of libbathygrid.so. Every entry point takes plain pointers and sizes,
+ * returns a bg_status, and never throws. All coordinates are int32
+ * centimetres, depths are float32 metres (positive down), and squared
+ * distances are exact int64 cm^2.
+ *
+ * The method (arXiv 2505.22675, "Towards Real-Time Interpolation for
+ * Enhanced AUV Deep Sea Mapping"):
+ *   - each grid node gathers its nearest valid soundings (Sec. III-D: "nearest
+ *     n valid candidate neighbors"; valid = depth not NaN, Sec. III-B);
+ *   - from them it computes an inverse-distance-weighted estimate or an
+ *     ordinary-kriging estimate (Sec. III-C: variogram equation, kriging
+ *     system, estimate equation) with its kriging variance.
+ * Neighbours are exact: the k smallest (d2, upload index) pairs, ties broken
+ * by the lower upload index, returned in ascending order.
+ *
+ * Ownership: the library owns everything it allocates (sorted soundings,
+ * spatial hash, queues); the caller owns input and output buffers. Errors:
+ * outputs are undefined when a call fails; bg_last_error() gives a message
+ * for the calling thread. Handles are thread-compatible (one thread at a time
+ * per handle); the serving calls (bg_submit / bg_poll / bg_wait) are
+ * thread-safe on one context.
+ */
+#ifndef BATHYGRID_H
+#define BATHYGRID_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum bg_status {
+    BG_OK = 0,
+    BG_PENDING = 1,            /* bg_poll: the ticket has not finished yet */
+    BG_ERR_INVALID_ARG = -1,   /* a null pointer, a size out of range, a bad handle */
+    BG_ERR_OOM_BUDGET = -2,    /* the context's HBM budget would be exceeded */
+    BG_ERR_CUDA = -3,          /* a CUDA runtime call failed (message in bg_last_error) */
+    BG_ERR_TIMEOUT = -4,       /* bg_wait ran out of time, or a device wait gave up */
+    BG_ERR_CANCELLED = -5,     /* the ticket was cancelled */
+    BG_ERR_INTERNAL = -6,      /* a device-side check failed (message in bg_last_error) */
+    BG_ERR_NOT_FOUND = -7      /* unknown ticket */
+} bg_status;
+
+typedef struct bg_ctx_s* bg_ctx_t;
+typedef struct bg_grid_s* bg_grid_t;
+typedef struct bg_soundings_s* bg_soundings_t;
+
+/* Variogram models. Spherical: gamma(h) = c0 + c (1.5 h/a - 0.5 (h/a)^3) for
+ * 0 < h <= a and c0 + c beyond. Exponential (the model printed in Sec. III-C,
+ * variogram equation): gamma(h) = c0 + c (1 - exp(-h/a)). c0 = nugget,
+ * c0 + c = sill (the TOTAL sill), a = range, h in metres. gamma(0) = 0 for a
+ * sounding with itself and for a node on top of a sounding; two distinct
+ * soundings at one position get c0. */
+typedef enum bg_variogram_model {
+    BG_VARIOGRAM_SPHERICAL = 0,
+    BG_VARIOGRAM_EXPONENTIAL = 1
+} bg_variogram_model;
+
+typedef struct bg_variogram {
+    int32_t model;     /* bg_variogram_model */
+    float nugget_m2;   /* c0 >= 0 */
+    float sill_m2;     /* total sill c0 + c, > c0 */
+    float range_m;     /* a > 0 */
+} bg_variogram;
+
+typedef struct bg_soundings_info {
+    int64_t n_total;        /* soundings passed to bg_soundings_upload */
+    int64_t n_valid;        /* of them with a non-NaN depth */
+    int32_t bbox_x0_cm, bbox_y0_cm;   /* min x, min y over valid soundings */
+    int32_t bbox_x1_cm, bbox_y1_cm;   /* max x, max y over valid soundings (inclusive) */
+    int32_t cell_cm;        /* spatial-hash cell side */
+    int32_t ncx, ncy;       /* hash cells along x and y */
+    int64_t device_bytes;   /* device memory held by this handle */
+} bg_soundings_info;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on CUDA device `device` that may hold at most
+ * `hbm_budget_bytes` of device memory (0 = no limit). Allocations that would
+ * exceed the budget fail with BG_ERR_OOM_BUDGET. */
+bg_status bg_ctx_create(int device, size_t hbm_budget_bytes, bg_ctx_t* out);
+
+/* Destroy a context. Every grid and soundings handle made from it must have
+ * been destroyed; pending serving tickets are cancelled and drained. */
+bg_status bg_ctx_destroy(bg_ctx_t ctx);
+
+/* Bytes of device memory the context holds now. */
+bg_status bg_ctx_device_bytes(bg_ctx_t ctx, int64_t* out);
+
+/* ------------------------------------------------------------------- grid */
+
+/* Describe a regular output grid of nx * ny nodes. Node (i, j) sits at the
+ * pixel centre (x0 + i*cell + cell/2, y0 + j*cell + cell/2) cm; outputs are
+ * row-major, index j*nx + i. cell_cm must be even and > 0 so that node
+ * coordinates are integers; every node coordinate must lie in
+ * (-2^30, 2^30), and nx * ny <= 2^36. */
+bg_status bg_grid_create(bg_ctx_t ctx, int32_t x0_cm, int32_t y0_cm, int32_t cell_cm,
+                         int32_t nx, int32_t ny, bg_grid_t* out);
+bg_status bg_grid_destroy(bg_grid_t grid);
+
+/* -------------------------------------------------------------- soundings */
+
+/* Upload n soundings and build the device spatial hash (a counting sort of
+ * the valid soundings into uniform cells, Sec. III-D's neighbour helper made
+ * exact).
+ *   x_cm, y_cm, z_m: n values each; device pointers if on_device != 0, else
+ *     host pointers (pageable or pinned), copied before the call returns.
+ *     Soundings with NaN depth are dropped ("valid" neighbours, Sec. III-B).
+ *     Valid coordinates must lie in (-2^30, 2^30); n < 2^31 - 1.
+ *   cell_cm_hint: hash cell side in cm; 0 picks one from the data density.
+ *     Results do not depend on it (neighbour search is exact), only speed.
+ *   cuda_stream: cudaStream_t (NULL = legacy default stream). The call
+ *     synchronizes this stream once to read the bounding box; the rest of
+ *     the build is enqueued on it.
+ * The handle keeps its own copy; the input buffers may be reused on return. */
+bg_status bg_soundings_upload(bg_ctx_t ctx, const int32_t* x_cm, const int32_t* y_cm,
+                              const float* z_m, int64_t n, int on_device, int32_t cell_cm_hint,
+                              void* cuda_stream, bg_soundings_t* out);
+bg_status bg_soundings_info_get(bg_soundings_t s, bg_soundings_info* out);
+bg_status bg_soundings_destroy(bg_soundings_t s);
+
+/* --------------------------------------------------------- interpolation */
+
+/* Inverse-distance weighting over the k nearest valid soundings:
+ * zhat = sum w_i z_i / sum w_i, w_i = d_i^-power. A node on top of a
+ * sounding returns that sounding's depth (lowest upload index first). With
+ * k_eff = min(k, n_valid) neighbours; no valid sounding gives NaN.
+ *   k in [1, 32]; power > 0.
+ *   depth_out: device, nx*ny float32, row-major.
+ *   nbr_out: NULL or device nx*ny*k int32: the neighbours' upload indices in
+ *     ascending (d2, index) order, -1 beyond k_eff.
+ * Asynchronous on cuda_stream; the caller synchronizes. */
+bg_status bg_interp_idw(bg_soundings_t s, bg_grid_t grid, int k, float power,
+                        float* depth_out, int32_t* nbr_out, void* cuda_stream);
+
+/* Local ordinary kriging over the k nearest valid soundings (Sec. III-C):
+ * solves [Gamma 1; 1^T 0][lambda; mu] = [gamma_0; 1], returns
+ * zhat = sum lambda_i z_i (Sec. III-C, estimate equation) and the kriging
+ * variance sigma^2 = sum lambda_i gamma_i0 + mu. The system is solved in
+ * FP32 with one step of iterative refinement whose residual is accumulated
+ * in FP64; the weight sum is closed in FP64.
+ *   k in [1, 32]; v: variogram (see bg_variogram).
+ *   depth_out, var_out: device, nx*ny float32 each (var_out may be NULL).
+ *   nbr_out: as for bg_interp_idw.
+ * A node with no valid sounding gets NaN. Asynchronous on cuda_stream. */
+bg_status bg_interp_okrige(bg_soundings_t s, bg_grid_t grid, int k, const bg_variogram* v,
+                           float* depth_out, float* var_out, int32_t* nbr_out,
+                           void* cuda_stream);
+
+/* ---------------------------------------------------------------- errors */
+
+const char* bg_status_str(bg_status st);
+/* Message for the last failed call on this thread ("" if none). */
+const char* bg_last_error(void);
+/* Library version string. */
+const char* bg_version(void);
+/* Number of CUDA kernels this library has launched since it was loaded
+ * (all threads, all contexts); a diagnostic for benchmarks. */
+bg_status bg_launch_count(uint64_t* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BATHYGRID_H */

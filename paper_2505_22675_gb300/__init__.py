@@ -1,0 +1,164 @@
+"""bathygrid: gridding scattered multibeam soundings on a GB300 GPU.
+
+Thin Python binding of libbathygrid.so (include/bathygrid.h). Functions keep
+the C names without the `bg_` prefix and only marshal arguments: every step
+of the hot path (hash build, neighbour search, IDW, kriging) runs in the
+library's CUDA kernels. PyTorch supplies device memory and streams.
+
+    ctx = ctx_create(0)
+    grid = grid_create(ctx, 0, 0, 200, 256, 256)
+    s = soundings_upload(ctx, x_cm, y_cm, z_m)        # torch tensors or numpy arrays
+    depth = torch.empty(256 * 256, device="cuda")
+    interp_idw(s, grid, 8, 2.0, depth)
+"""
+from __future__ import annotations
+
+import ctypes
+
+from . import _capi
+from ._capi import BGError, SoundingsInfo, Variogram, check
+
+SPHERICAL = 0
+EXPONENTIAL = 1
+IDW = 0
+OKRIGE = 1
+
+__all__ = [
+    "BGError", "Variogram", "SoundingsInfo", "SPHERICAL", "EXPONENTIAL", "IDW", "OKRIGE",
+    "version", "launch_count", "ctx_create", "ctx_destroy", "ctx_device_bytes", "grid_create", "grid_destroy",
+    "soundings_upload", "soundings_info", "soundings_destroy", "interp_idw", "interp_okrige",
+    "variogram",
+]
+
+
+def _lib():
+    return _capi.load()
+
+
+def _ptr(t):
+    """Raw address of a torch tensor or numpy array (None -> NULL)."""
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        if not t.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(t.data_ptr())
+    return ctypes.c_void_p(t.ctypes.data)
+
+
+def _is_cuda(t):
+    return t is not None and getattr(t, "is_cuda", False)
+
+
+def _stream(stream, *tensors):
+    """cudaStream_t for the call: explicit, else torch's current stream when a
+    tensor lives on the GPU, else NULL (legacy default stream)."""
+    if stream is not None:
+        return ctypes.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
+    for t in tensors:
+        if _is_cuda(t):
+            import torch
+            return ctypes.c_void_p(torch.cuda.current_stream(t.device).cuda_stream)
+    return ctypes.c_void_p(0)
+
+
+def version() -> str:
+    return _lib().bg_version().decode()
+
+
+def launch_count() -> int:
+    """Kernels the library has launched since it was loaded."""
+    out = ctypes.c_uint64()
+    check(_lib().bg_launch_count(ctypes.byref(out)), "bg_launch_count")
+    return out.value
+
+
+def variogram(model: int = SPHERICAL, nugget_m2: float = 0.25, sill_m2: float = 100.0,
+              range_m: float = 50.0) -> Variogram:
+    """Variogram parameters; sill is the total sill (nugget + partial sill)."""
+    return Variogram(model, nugget_m2, sill_m2, range_m)
+
+
+def ctx_create(device: int = 0, hbm_budget_bytes: int = 0):
+    out = ctypes.c_void_p()
+    check(_lib().bg_ctx_create(device, hbm_budget_bytes, ctypes.byref(out)), "bg_ctx_create")
+    return out
+
+
+def ctx_destroy(ctx) -> None:
+    check(_lib().bg_ctx_destroy(ctx), "bg_ctx_destroy")
+
+
+def ctx_device_bytes(ctx) -> int:
+    out = ctypes.c_int64()
+    check(_lib().bg_ctx_device_bytes(ctx, ctypes.byref(out)), "bg_ctx_device_bytes")
+    return out.value
+
+
+def grid_create(ctx, x0_cm: int, y0_cm: int, cell_cm: int, nx: int, ny: int):
+    out = ctypes.c_void_p()
+    check(_lib().bg_grid_create(ctx, x0_cm, y0_cm, cell_cm, nx, ny, ctypes.byref(out)),
+          "bg_grid_create")
+    return out
+
+
+def grid_destroy(grid) -> None:
+    check(_lib().bg_grid_destroy(grid), "bg_grid_destroy")
+
+
+def soundings_upload(ctx, x_cm, y_cm, z_m, cell_cm_hint: int = 0, stream=None):
+    """Upload soundings (int32 cm, int32 cm, float32 m) and build the device hash.
+
+    Device tensors are read in place; host tensors / numpy arrays are copied.
+    """
+    on_dev = [_is_cuda(t) for t in (x_cm, y_cm, z_m)]
+    if any(on_dev) and not all(on_dev):
+        raise ValueError("x, y and z must all be on the device or all on the host")
+    n = int(x_cm.shape[0])
+    if int(y_cm.shape[0]) != n or int(z_m.shape[0]) != n:
+        raise ValueError("x, y and z must have the same length")
+    _check_dtype(x_cm, "int32")
+    _check_dtype(y_cm, "int32")
+    _check_dtype(z_m, "float32")
+    out = ctypes.c_void_p()
+    check(_lib().bg_soundings_upload(ctx, _ptr(x_cm), _ptr(y_cm), _ptr(z_m), n, int(all(on_dev)),
+                                     cell_cm_hint, _stream(stream, x_cm), ctypes.byref(out)),
+          "bg_soundings_upload")
+    return out
+
+
+def soundings_info(s) -> SoundingsInfo:
+    info = SoundingsInfo()
+    check(_lib().bg_soundings_info_get(s, ctypes.byref(info)), "bg_soundings_info_get")
+    return info
+
+
+def soundings_destroy(s) -> None:
+    check(_lib().bg_soundings_destroy(s), "bg_soundings_destroy")
+
+
+def interp_idw(s, grid, k: int, power: float, depth_out, nbr_out=None, stream=None) -> None:
+    """IDW over the k nearest valid soundings into depth_out (device, nx*ny float32)."""
+    _check_dtype(depth_out, "float32")
+    if nbr_out is not None:
+        _check_dtype(nbr_out, "int32")
+    check(_lib().bg_interp_idw(s, grid, k, power, _ptr(depth_out), _ptr(nbr_out),
+                               _stream(stream, depth_out)), "bg_interp_idw")
+
+
+def interp_okrige(s, grid, k: int, vgm: Variogram, depth_out, var_out=None, nbr_out=None,
+                  stream=None) -> None:
+    """Ordinary kriging over the k nearest valid soundings (depth and variance)."""
+    _check_dtype(depth_out, "float32")
+    if var_out is not None:
+        _check_dtype(var_out, "float32")
+    if nbr_out is not None:
+        _check_dtype(nbr_out, "int32")
+    check(_lib().bg_interp_okrige(s, grid, k, ctypes.byref(vgm), _ptr(depth_out), _ptr(var_out),
+                                  _ptr(nbr_out), _stream(stream, depth_out)), "bg_interp_okrige")
+
+
+def _check_dtype(t, name):
+    dt = str(t.dtype)
+    if not dt.endswith(name):
+        raise TypeError(f"expected {name}, got {dt}")

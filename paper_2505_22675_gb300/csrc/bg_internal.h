@@ -1,0 +1,120 @@
+// Internal types shared by the host side of libbathygrid and its kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <mutex>
+#include <string>
+
+#include "bathygrid.h"
+
+namespace bg {
+
+// ------------------------------------------------------------------ errors
+
+void set_error(const std::string& msg);
+bg_status cuda_fail(cudaError_t e, const char* what);
+
+// Kernel launches made by this library since load (bg_launch_count).
+extern std::atomic<uint64_t> g_launches;
+inline void note_launches(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
+
+#define BG_CUDA(call)                                      \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return bg::cuda_fail(e_, #call); \
+    } while (0)
+
+// -------------------------------------------------------------- device views
+
+// Cell-sorted soundings plus the lookup tables of the uniform-cell hash.
+// Passed by value to kernels.
+struct HashView {
+    const int4* rec;          // [n_valid] cell-sorted {x_cm, y_cm, z bits, upload index}
+    const int4* orig;         // [n_total] upload order {x_cm, y_cm, z bits, valid}
+    const int32_t* cell_start;// [ncx*ncy + 1] first record of each cell (row-major cells)
+    const int32_t* sat;       // [(ncy+1)*(ncx+1)] summed-area table of per-cell counts
+    int32_t hx0, hy0;         // hash origin (cm) = bbox min
+    int32_t cs;               // cell side (cm)
+    float inv_cs;             // 1 / cs
+    int32_t ncx, ncy;
+    int32_t n_valid;
+    int32_t idx_bits;         // bits that hold an upload index in a packed key
+    int32_t r0;               // first square half-width (cells) tried by the bound search
+};
+
+struct GridView {
+    int32_t x0, y0, cell, nx, ny;
+};
+
+struct OkParams {
+    int32_t model;
+    float c0;      // nugget
+    float c;       // partial sill = sill - nugget
+    float sill;    // total sill
+    float inv_a;   // 1 / range (1/m)
+};
+
+// ---------------------------------------------------------------- handles
+
+struct Ctx;
+
+struct DevBuf {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace bg
+
+struct bg_ctx_s {
+    int device = 0;
+    size_t budget = 0;                 // 0 = unlimited
+    std::atomic<int64_t> in_use{0};
+    std::mutex mu;
+    cudaMemPool_t pool = nullptr;      // stream-ordered pool owned by the context
+    std::mutex pin_mu;                 // guards h_pinned
+    int32_t* h_pinned = nullptr;       // pinned host scratch for the bbox read-back
+    int n_grids = 0, n_soundings = 0;
+    struct Server* server = nullptr;   // serving state (lazily created)
+};
+
+struct bg_grid_s {
+    bg_ctx_s* ctx;
+    bg::GridView g;
+};
+
+struct bg_soundings_s {
+    bg_ctx_s* ctx;
+    bg_soundings_info info;
+    bg::HashView h;
+    void* d_orig = nullptr;
+    void* d_rec = nullptr;
+    void* d_cell_start = nullptr;
+    void* d_sat = nullptr;
+    size_t bytes = 0;
+};
+
+namespace bg {
+
+// Budgeted stream-ordered allocation (cudaMallocAsync) charged to a context.
+bg_status dalloc(bg_ctx_s* ctx, void** p, size_t bytes, cudaStream_t st);
+void dfree(bg_ctx_s* ctx, void* p, size_t bytes, cudaStream_t st);
+
+// Hash build: validate + pack + bbox, then counting sort and lookup tables.
+bg_status build_soundings(bg_ctx_s* ctx, const int32_t* x, const int32_t* y, const float* z,
+                          int64_t n, int on_device, int32_t cell_hint, cudaStream_t st,
+                          bg_soundings_s* s);
+
+// Start half-width (cells) for the k-NN bound search at this k.
+int32_t start_halfwidth(const bg_soundings_s* s, int k);
+
+// Each call allocates (stream-ordered) a one-int flag that tells the wide-key
+// pass whether the packed pass left nodes for it.
+bg_status launch_idw(const bg_soundings_s* s, const GridView& g, int k, float power,
+                     float* depth, int32_t* nbr, cudaStream_t st);
+bg_status launch_okrige(const bg_soundings_s* s, const GridView& g, int k, const OkParams& p,
+                        float* depth, float* var, int32_t* nbr, cudaStream_t st);
+
+}  // namespace bg

@@ -1,0 +1,143 @@
+// Fused exact k-NN + inverse-distance weighting, one thread per grid node.
+//
+// zhat = sum w_i z_i / sum w_i with w_i = d_i^-p over the k nearest valid
+// soundings. It is evaluated as z_1 + sum w_i (z_i - z_1) / sum w_i with
+// z_1 the nearest sounding's depth and w_i = (d_1^2 / d_i^2)^(p/2): the same
+// quantity, but every term is an anomaly of a few metres (so only the final
+// add rounds at ~3500 m) and every weight is in (0, 1]. Accumulation follows
+// the ascending (d2, index) order, so a node's result does not depend on the
+// cell size, the launch shape or what else runs.
+#include <algorithm>
+#include <cmath>
+
+#include "bg_internal.h"
+#include "knn.cuh"
+
+namespace bg {
+namespace {
+
+template <int K, bool kWide>
+__device__ __forceinline__ void idw_node(const HashView& h, const GridView& g, int k, float power,
+                                         float* __restrict__ depth, int32_t* __restrict__ nbr,
+                                         int* __restrict__ flag, NodeIdx nd) {
+    if (nd.i >= g.nx || nd.j >= g.ny) return;
+    const int64_t node = (int64_t)nd.j * g.nx + nd.i;
+    const int qx = g.x0 + nd.i * g.cell + g.cell / 2;
+    const int qy = g.y0 + nd.j * g.cell + g.cell / 2;
+
+    uint64_t d2[K];
+    int id[K];
+    int keff = 0;
+    if (h.n_valid > 0) {
+        const Bound b = knn_bound<K>(h, qx, qy);
+        const bool fits = packed_fits(h, b.tau0);
+        if (kWide) {
+            if (fits) return;  // done by the packed pass
+        } else if (!fits) {
+            *flag = 1;  // the wide pass picks this node up
+            return;
+        }
+        keff = knn_scan<K, kWide>(h, qx, qy, b, d2, id);
+    } else if (kWide) {
+        return;
+    } else {
+#pragma unroll
+        for (int i = 0; i < K; ++i) id[i] = -1;
+    }
+    if (keff > k) keff = k;
+
+    float out;
+    if (keff == 0) {
+        out = __int_as_float(0x7fc00000);  // NaN: no valid sounding
+    } else {
+        const int* zb = reinterpret_cast<const int*>(h.orig) + 2;  // z bits of record i at zb[4*i]
+        const float z1 = __int_as_float(__ldg(zb + 4 * (int64_t)id[0]));
+        if (d2[0] == 0) {
+            out = z1;  // node on top of a sounding
+        } else {
+            const float d1 = (float)d2[0];
+            const float l1 = log2f(d1);
+            const float hp = 0.5f * power;
+            float num = 0.0f, den = 1.0f;  // i = 0 contributes w = 1, anomaly 0
+#pragma unroll
+            for (int i = 1; i < K; ++i) {
+                if (i < keff) {
+                    const float zi = __int_as_float(__ldg(zb + 4 * (int64_t)id[i]));
+                    const float di = (float)d2[i];
+                    const float w = (power == 2.0f) ? d1 / di : exp2f(hp * (l1 - log2f(di)));
+                    num = fmaf(w, zi - z1, num);
+                    den += w;
+                }
+            }
+            out = z1 + num / den;
+        }
+    }
+    depth[node] = out;
+    if (nbr) {
+        int32_t* o = nbr + node * k;
+#pragma unroll
+        for (int i = 0; i < K; ++i)
+            if (i < k) o[i] = i < keff ? id[i] : -1;
+    }
+}
+
+// Packed pass: one 16 x 8 node patch per block.
+template <int K>
+__global__ void __launch_bounds__(128) k_idw(HashView h, GridView g, int k, float power,
+                                             float* __restrict__ depth,
+                                             int32_t* __restrict__ nbr, int* __restrict__ flag) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int gx = (g.nx + 15) / 16;
+    idw_node<K, false>(h, g, k, power, depth, nbr, flag,
+                       patch_node(blockIdx.x % gx, blockIdx.x / gx, warp, lane));
+}
+
+// Wide-key pass over the nodes the packed pass could not take; it returns at
+// once when the packed pass flagged none.
+template <int K>
+__global__ void __launch_bounds__(128) k_idw_wide(HashView h, GridView g, int k, float power,
+                                                  float* __restrict__ depth,
+                                                  int32_t* __restrict__ nbr, int* __restrict__ flag) {
+    if (*(volatile int*)flag == 0) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int gx = (g.nx + 15) / 16;
+    const int64_t nb = (int64_t)gx * ((g.ny + 7) / 8);
+    for (int64_t b = blockIdx.x; b < nb; b += gridDim.x)
+        idw_node<K, true>(h, g, k, power, depth, nbr, flag,
+                          patch_node((int)(b % gx), (int)(b / gx), warp, lane));
+}
+
+template <int K>
+bg_status launch_k(const HashView& h, const GridView& g, int k, float power, float* depth,
+                   int32_t* nbr, int* d_flag, cudaStream_t st) {
+    const int64_t nb = (int64_t)((g.nx + 15) / 16) * ((g.ny + 7) / 8);
+    BG_CUDA(cudaMemsetAsync(d_flag, 0, sizeof(int), st));
+    k_idw<K><<<(unsigned)nb, 128, 0, st>>>(h, g, k, power, depth, nbr, d_flag);
+    k_idw_wide<K><<<(unsigned)std::min<int64_t>(nb, 152 * 4), 128, 0, st>>>(h, g, k, power, depth,
+                                                                        nbr, d_flag);
+    note_launches(2);
+    BG_CUDA(cudaGetLastError());
+    return BG_OK;
+}
+
+}  // namespace
+
+bg_status launch_idw(const bg_soundings_s* s, const GridView& g, int k, float power,
+                     float* depth, int32_t* nbr, cudaStream_t st) {
+    HashView h = s->h;
+    const int K = k <= 4 ? 4 : k <= 8 ? 8 : k <= 16 ? 16 : 32;
+    h.r0 = start_halfwidth(s, K);
+    int* flag = nullptr;
+    bg_status rc = dalloc(s->ctx, (void**)&flag, sizeof(int), st);
+    if (rc != BG_OK) return rc;
+    switch (K) {
+        case 4: rc = launch_k<4>(h, g, k, power, depth, nbr, flag, st); break;
+        case 8: rc = launch_k<8>(h, g, k, power, depth, nbr, flag, st); break;
+        case 16: rc = launch_k<16>(h, g, k, power, depth, nbr, flag, st); break;
+        default: rc = launch_k<32>(h, g, k, power, depth, nbr, flag, st); break;
+    }
+    dfree(s->ctx, flag, sizeof(int), st);
+    return rc;
+}
+
+}  // namespace bg

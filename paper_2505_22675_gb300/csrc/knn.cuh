@@ -1,0 +1,227 @@
+// Exact k-nearest-neighbour search of one grid node over the device hash.
+//
+// The neighbours of a node are the K smallest keys (d2, upload index), with
+// d2 = dx^2 + dy^2 an exact int64 in cm^2 and ties broken by the lower upload
+// index (Sec. III-D's "nearest n valid candidate neighbors", made exact).
+//
+// Two phases, both per thread:
+//   1. Bound. With the summed-area table, find the smallest square of cells
+//      around the node's cell (half-width R) that holds at least K soundings
+//      (or the whole hash). Every sounding in that square is within tau0 =
+//      the squared distance to the square's farthest corner, so d_K^2 <= tau0.
+//   2. Scan. Visit rows of cells in order of their distance from the node,
+//      and in each row only the run of cells that can hold a point with
+//      d2 <= tau (one contiguous range of the cell-sorted records). tau starts
+//      at tau0 and drops to the current K-th key after every row; a row whose
+//      nearest edge is farther than tau ends that side. Every sounding with
+//      d2 <= d_K^2 is visited, so the result is exact.
+// Keys are packed as (d2 << idx_bits) | index in a uint64 when tau0 leaves
+// room for it (the usual case: tau0 < 2^(64 - idx_bits)); otherwise the wide
+// form keeps d2 and the index apart. Both give the same ordering.
+#pragma once
+
+#include <climits>
+#include <cstdint>
+
+#include "bg_internal.h"
+
+namespace bg {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// floor(off / cs) for 0 <= off < ncx*cs (exact: float estimate, integer fix-up)
+__device__ __forceinline__ int cell_of(const HashView& h, int64_t off) {
+    int c = (int)((float)off * h.inv_cs);
+    while ((int64_t)c * h.cs > off) --c;
+    while ((int64_t)(c + 1) * h.cs <= off) ++c;
+    return c;
+}
+
+// Node coordinate -> hash cell, clamped into the hash.
+__device__ __forceinline__ int clamp_cell(const HashView& h, int64_t off, int n) {
+    if (off < 0) return 0;
+    if (off >= (int64_t)n * h.cs) return n - 1;
+    return cell_of(h, off);
+}
+
+// An upper bound on floor(sqrt(v)) for 0 <= v < 2^62.
+__device__ __forceinline__ int64_t isqrt_ub(int64_t v) {
+    const float f = sqrtf((float)v);
+    return (int64_t)(f * 1.0000020f) + 1;
+}
+
+__device__ __forceinline__ int sat_count(const HashView& h, int xa, int ya, int xb, int yb) {
+    const int W = h.ncx + 1;
+    const int32_t* s = h.sat;
+    return __ldg(s + (yb + 1) * W + xb + 1) - __ldg(s + ya * W + xb + 1) -
+           __ldg(s + (yb + 1) * W + xa) + __ldg(s + ya * W + xa);
+}
+
+struct Bound {
+    int64_t tau0;   // d_K^2 <= tau0
+    int cy;         // the node's (clamped) cell row
+};
+
+// Phase 1: the smallest square around the node's cell holding >= K soundings.
+template <int K>
+__device__ __forceinline__ Bound knn_bound(const HashView& h, int qx, int qy) {
+    const int cx = clamp_cell(h, (int64_t)qx - h.hx0, h.ncx);
+    const int cy = clamp_cell(h, (int64_t)qy - h.hy0, h.ncy);
+    const int rmax = max(max(cx, h.ncx - 1 - cx), max(cy, h.ncy - 1 - cy));
+    auto cnt = [&](int r) {
+        return sat_count(h, max(cx - r, 0), max(cy - r, 0), min(cx + r, h.ncx - 1),
+                         min(cy + r, h.ncy - 1));
+    };
+    int r = min(h.r0, rmax);
+    int lo, hi;
+    if (cnt(r) >= K) {
+        lo = -1;
+        hi = r;
+    } else {
+        lo = r;
+        hi = r;
+        while (hi < rmax) {
+            hi = min(2 * hi + 1, rmax);
+            if (cnt(hi) >= K) break;
+            lo = hi;
+        }
+    }
+    while (hi - lo > 1) {  // invariant: cnt(lo) < K (or lo = -1), cnt(hi) >= K
+        const int mid = (lo + hi) >> 1;
+        if (cnt(mid) >= K)
+            hi = mid;
+        else
+            lo = mid;
+    }
+    const int xa = max(cx - hi, 0), xb = min(cx + hi, h.ncx - 1);
+    const int ya = max(cy - hi, 0), yb = min(cy + hi, h.ncy - 1);
+    const int64_t xlo = (int64_t)h.hx0 + (int64_t)xa * h.cs;
+    const int64_t xhi = (int64_t)h.hx0 + (int64_t)(xb + 1) * h.cs - 1;
+    const int64_t ylo = (int64_t)h.hy0 + (int64_t)ya * h.cs;
+    const int64_t yhi = (int64_t)h.hy0 + (int64_t)(yb + 1) * h.cs - 1;
+    const int64_t mdx = max((int64_t)qx - xlo, xhi - (int64_t)qx);
+    const int64_t mdy = max((int64_t)qy - ylo, yhi - (int64_t)qy);
+    return Bound{mdx * mdx + mdy * mdy, cy};
+}
+
+// Does (tau0 + 1) << idx_bits fit in 64 bits?
+__device__ __forceinline__ bool packed_fits(const HashView& h, int64_t tau0) {
+    return ((uint64_t)(tau0 + 1) >> (64 - h.idx_bits)) == 0;
+}
+
+template <int K>
+__device__ __forceinline__ void insert_packed(uint64_t (&key)[K], uint64_t c) {
+    // precondition: c < key[K-1]; keeps key[] ascending
+#pragma unroll
+    for (int j = K - 1; j > 0; --j) key[j] = (c < key[j - 1]) ? key[j - 1] : ((c < key[j]) ? c : key[j]);
+    key[0] = (c < key[0]) ? c : key[0];
+}
+
+__device__ __forceinline__ bool wide_less(uint64_t ad, int ai, uint64_t bd, int bi) {
+    return ad < bd || (ad == bd && ai < bi);
+}
+
+template <int K>
+__device__ __forceinline__ void insert_wide(uint64_t (&kd)[K], int (&ki)[K], uint64_t cd, int ci) {
+#pragma unroll
+    for (int j = K - 1; j > 0; --j) {
+        if (wide_less(cd, ci, kd[j - 1], ki[j - 1])) {
+            kd[j] = kd[j - 1];
+            ki[j] = ki[j - 1];
+        } else if (wide_less(cd, ci, kd[j], ki[j])) {
+            kd[j] = cd;
+            ki[j] = ci;
+        }
+    }
+    if (wide_less(cd, ci, kd[0], ki[0])) {
+        kd[0] = cd;
+        ki[0] = ci;
+    }
+}
+
+// Phase 2. On return d2o[0..keff) / ido[0..keff) hold the neighbours in
+// ascending (d2, index) order; returns keff (<= K).
+template <int K, bool kWide>
+__device__ __forceinline__ int knn_scan(const HashView& h, int qx, int qy, const Bound& b,
+                                        uint64_t (&d2o)[K], int (&ido)[K]) {
+    const int bits = h.idx_bits;
+    const int64_t tau0 = b.tau0;
+    uint64_t key[K];   // packed form (or the d2 half of the wide form)
+    int kid[kWide ? K : 1];
+    const uint64_t sentinel = kWide ? (uint64_t)(tau0 + 1) : ((uint64_t)(tau0 + 1) << bits);
+#pragma unroll
+    for (int i = 0; i < K; ++i) key[i] = sentinel;
+#pragma unroll
+    for (int i = 0; i < (kWide ? K : 1); ++i) kid[i] = INT_MAX;
+    int64_t tau = tau0;
+    int up = b.cy, dn = b.cy - 1;
+    const int64_t xmin = h.hx0;
+    const int64_t xmax = (int64_t)h.hx0 + (int64_t)h.ncx * h.cs - 1;
+    for (;;) {
+        int64_t dyu = LLONG_MAX, dyd = LLONG_MAX;
+        if (up < h.ncy) {
+            const int64_t ylo = (int64_t)h.hy0 + (int64_t)up * h.cs, yhi = ylo + h.cs - 1;
+            dyu = qy < ylo ? ylo - qy : (qy > yhi ? qy - yhi : 0);
+        }
+        if (dn >= 0) {
+            const int64_t ylo = (int64_t)h.hy0 + (int64_t)dn * h.cs, yhi = ylo + h.cs - 1;
+            dyd = qy < ylo ? ylo - qy : (qy > yhi ? qy - yhi : 0);
+        }
+        const bool take_up = dyu <= dyd;
+        const int64_t dy = take_up ? dyu : dyd;
+        if (dy == LLONG_MAX || dy * dy > tau) break;
+        const int row = take_up ? up++ : dn--;
+        const int64_t dxm = isqrt_ub(tau - dy * dy);
+        const int64_t xa = max((int64_t)qx - dxm, xmin), xb = min((int64_t)qx + dxm, xmax);
+        if (xa > xb) continue;
+        const int ca = cell_of(h, xa - h.hx0), cb = cell_of(h, xb - h.hx0);
+        const int rowbase = row * h.ncx;
+        const int s = __ldg(h.cell_start + rowbase + ca);
+        const int e = __ldg(h.cell_start + rowbase + cb + 1);
+        const uint64_t utau = (uint64_t)tau;
+        for (int p = s; p < e; ++p) {
+            const int4 v = __ldg(h.rec + p);
+            const int ddx = v.x - qx, ddy = v.y - qy;
+            const uint64_t d2 = (uint64_t)((long long)ddx * ddx + (long long)ddy * ddy);
+            if (d2 > utau) continue;
+            if constexpr (kWide) {
+                if (wide_less(d2, v.w, key[K - 1], kid[K - 1])) insert_wide<K>(key, kid, d2, v.w);
+            } else {
+                const uint64_t c = (d2 << bits) | (uint32_t)v.w;
+                if (c < key[K - 1]) insert_packed<K>(key, c);
+            }
+        }
+        int64_t kth;
+        if constexpr (kWide)
+            kth = (int64_t)key[K - 1];
+        else
+            kth = (int64_t)(key[K - 1] >> bits);
+        tau = min(tau, kth);
+    }
+    int keff = 0;
+    const uint64_t mask = (bits >= 64) ? ~0ull : ((1ull << bits) - 1);
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+        const bool ok = key[i] < sentinel;  // every real key has d2 <= tau0
+        if constexpr (kWide) {
+            d2o[i] = key[i];
+            ido[i] = ok ? kid[i] : -1;
+        } else {
+            d2o[i] = key[i] >> bits;
+            ido[i] = ok ? (int)(key[i] & mask) : -1;
+        }
+        keff += ok ? 1 : 0;
+    }
+    return keff;
+}
+
+// Grid node (i, j) owned by this thread inside the 16 x 8 node patch (px, py).
+// Each warp covers 8 x 4 nodes, so a warp's nodes are spatially compact.
+struct NodeIdx {
+    int i, j;
+};
+__device__ __forceinline__ NodeIdx patch_node(int px, int py, int warp, int lane) {
+    return NodeIdx{px * 16 + (warp & 1) * 8 + (lane & 7), py * 8 + (warp >> 1) * 4 + (lane >> 3)};
+}
+
+}  // namespace bg

@@ -1,0 +1,77 @@
+"""Parity at the benchmark's full size: the 4-line survey swath (20.48M
+soundings, 20,000 x 3,692 nodes at 0.5 m), IDW k=16 and kriging k=32, in the
+launch configuration bench.py times. The GPU grids every node; the oracle
+recomputes a sample of nodes one by one (swath interior, swath edges, the
+inter-line gaps and the grid border) by brute force.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_util import assert_idw, assert_okrige
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+
+@pytest.fixture(scope="module")
+def swath_run():
+    import torch
+
+    import paper_2505_22675_gb300 as bg
+    w = synth.swath()
+    g = w.grid
+    dev = torch.device("cuda:0")
+    ctx = bg.ctx_create(0)
+    grid = bg.grid_create(ctx, g.x0_cm, g.y0_cm, g.cell_cm, g.nx, g.ny)
+    x, y, z = (torch.from_numpy(a).to(dev) for a in (w.x_cm, w.y_cm, w.z_m))
+    s = bg.soundings_upload(ctx, x, y, z)
+    rng = np.random.default_rng(11)
+    sel = np.concatenate([
+        rng.choice(g.m, 300, replace=False),                         # anywhere
+        np.arange(0, g.nx, 997),                                     # first row (grid border)
+        (g.ny - 1) * g.nx + np.arange(3, g.nx, 1009),                # last row
+        rng.integers(0, g.nx, 60) + g.nx * rng.integers(700, 1000, 60),   # gap between lines 1 and 2
+    ]).astype(np.int64)
+    sel_t = torch.from_numpy(sel).to(dev)
+    out = {}
+    d = torch.empty(g.m, device=dev)
+    nb = torch.empty(g.m * 16, dtype=torch.int32, device=dev)
+    bg.interp_idw(s, grid, 16, 2.0, d, nb)
+    out["idw"] = (d[sel_t].cpu().numpy(), nb.view(g.m, 16)[sel_t].cpu().numpy(),
+                  int(torch.isnan(d).sum()))
+    del d, nb
+    d = torch.empty(g.m, device=dev)
+    v = torch.empty(g.m, device=dev)
+    nb = torch.empty(g.m * 32, dtype=torch.int32, device=dev)
+    bg.interp_okrige(s, grid, 32, bg.variogram(0, 0.25, 100.0, 50.0), d, v, nb)
+    out["ok"] = (d[sel_t].cpu().numpy(), v[sel_t].cpu().numpy(),
+                 nb.view(g.m, 32)[sel_t].cpu().numpy(), int(torch.isnan(d).sum()),
+                 float(v.min()))
+    del d, v, nb
+    torch.cuda.synchronize()
+    bg.soundings_destroy(s)
+    bg.grid_destroy(grid)
+    bg.ctx_destroy(ctx)
+    qx = (g.x0_cm + (sel % g.nx) * g.cell_cm + g.cell_cm // 2).astype(np.int32)
+    qy = (g.y0_cm + (sel // g.nx) * g.cell_cm + g.cell_cm // 2).astype(np.int32)
+    return w, qx, qy, out
+
+
+def test_swath_idw_k16(swath_run):
+    w, qx, qy, out = swath_run
+    d, nb, n_nan = out["idw"]
+    assert n_nan == 0
+    ref, ridx = oracle.idw(w.x_cm, w.y_cm, w.z_m, qx, qy, 16, 2.0, want_idx=True)
+    assert np.array_equal(nb, ridx)
+    assert_idw(d, ref)
+
+
+def test_swath_okrige_k32(swath_run):
+    w, qx, qy, out = swath_run
+    d, v, nb, n_nan, vmin = out["ok"]
+    assert n_nan == 0 and vmin >= -1e-3
+    rd, rv, ridx = oracle.okrige(w.x_cm, w.y_cm, w.z_m, qx, qy, 32, 0, 0.25, 100.0, 50.0,
+                                 want_idx=True)
+    assert np.array_equal(nb, ridx)
+    assert_okrige(d, v, rd, rv, 0.25)
