@@ -27,7 +27,7 @@ __all__ = [
     "BGError", "Variogram", "SoundingsInfo", "SPHERICAL", "EXPONENTIAL", "IDW", "OKRIGE",
     "version", "launch_count", "ctx_create", "ctx_destroy", "ctx_device_bytes", "grid_create", "grid_destroy",
     "soundings_upload", "soundings_info", "soundings_destroy", "interp_idw", "interp_okrige",
-    "variogram",
+    "variogram", "interp_idw_noalloc",
 ]
 
 
@@ -156,6 +156,25 @@ def interp_okrige(s, grid, k: int, vgm: Variogram, depth_out, var_out=None, nbr_
         _check_dtype(nbr_out, "int32")
     check(_lib().bg_interp_okrige(s, grid, k, ctypes.byref(vgm), _ptr(depth_out), _ptr(var_out),
                                   _ptr(nbr_out), _stream(stream, depth_out)), "bg_interp_okrige")
+
+
+def interp_idw_noalloc(x_cm, y_cm, z_m, grid_spec, k: int, power: float, depth_out,
+                      nbr_out=None, stream=None) -> None:
+    """IDW without any device allocation (device inputs, at most 262,144 soundings).
+
+    grid_spec = (x0_cm, y0_cm, cell_cm, nx, ny). For callers that cannot
+    allocate device memory; the library's fixed 16 MiB device array serves as
+    work space, so two overlapping calls must not run at once.
+    """
+    for t, dt in ((x_cm, "int32"), (y_cm, "int32"), (z_m, "float32"), (depth_out, "float32")):
+        _check_dtype(t, dt)
+    if nbr_out is not None:
+        _check_dtype(nbr_out, "int32")
+    x0, y0, cell, nx, ny = (int(v) for v in grid_spec)
+    check(_lib().bg_interp_idw_noalloc(_ptr(x_cm), _ptr(y_cm), _ptr(z_m), int(x_cm.shape[0]),
+                                       x0, y0, cell, nx, ny, k, power, _ptr(depth_out),
+                                       _ptr(nbr_out), _stream(stream, depth_out)),
+          "bg_interp_idw_noalloc")
 
 
 def _check_dtype(t, name):

@@ -80,6 +80,9 @@ _SIGNATURES = {
     "bg_interp_idw": ([P, P, ctypes.c_int, ctypes.c_float, P, P, P], ctypes.c_int),
     "bg_interp_okrige": ([P, P, ctypes.c_int, ctypes.POINTER(Variogram), P, P, P, P],
                          ctypes.c_int),
+    "bg_interp_idw_noalloc": ([P, P, P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                               ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int,
+                               ctypes.c_float, P, P, P], ctypes.c_int),
 }
 
 

@@ -110,6 +110,28 @@ bg_status build_soundings(bg_ctx_s* ctx, const int32_t* x, const int32_t* y, con
 // Start half-width (cells) for the k-NN bound search at this k.
 int32_t start_halfwidth(const bg_soundings_s* s, int k);
 
+// Device memory carved by the caller for a hash build that allocates nothing.
+struct HashArena {
+    int4* orig;          // n_max records
+    int4* rec;           // n_max records
+    int32_t* cell_start; // cells_max + 1
+    int32_t* count;      // cells_max
+    int32_t* sat;        // sat_max
+    int32_t* bsum;       // bsum_max
+    int32_t* csum;       // csum_max
+    int32_t* acc;        // 8
+    int64_t n_max, cells_max, sat_max, bsum_max, csum_max;
+};
+
+// The same hash build as build_soundings, into arena memory. Synchronizes the
+// stream once (bounding box) through a pageable host buffer.
+bg_status build_hash_in_arena(const int32_t* x, const int32_t* y, const float* z, int64_t n,
+                              const HashArena& ar, cudaStream_t st, bg_soundings_s* s);
+
+// IDW launch with a caller-provided device flag (one int) instead of an allocated one.
+bg_status launch_idw_with_flag(const bg_soundings_s* s, const GridView& g, int k, float power,
+                               float* depth, int32_t* nbr, int* d_flag, cudaStream_t st);
+
 // Each call allocates (stream-ordered) a one-int flag that tells the wide-key
 // pass whether the packed pass left nodes for it.
 bg_status launch_idw(const bg_soundings_s* s, const GridView& g, int k, float power,

@@ -443,4 +443,92 @@ int32_t start_halfwidth(const bg_soundings_s* s, int k) {
     return r > rmax ? rmax : r;
 }
 
+bg_status build_hash_in_arena(const int32_t* x, const int32_t* y, const float* z, int64_t n,
+                              const HashArena& ar, cudaStream_t st, bg_soundings_s* s) {
+    s->info = bg_soundings_info{};
+    s->info.n_total = n;
+    s->h = HashView{};
+    int bits = 1;
+    while (bits < 62 && (int64_t(1) << bits) < n) ++bits;
+    s->h.idx_bits = bits;
+    if (n > ar.n_max) {
+        set_error("too many soundings for the arena");
+        return BG_ERR_INVALID_ARG;
+    }
+    s->h.orig = ar.orig;
+    k_bbox_init<<<1, 32, 0, st>>>(ar.acc);
+    note_launches(1);
+    if (n > 0) {
+        k_validate_pack<<<grid_for(n, kThreads * 4, 152 * 16), kThreads, 0, st>>>(x, y, z, n,
+                                                                                ar.orig, ar.acc);
+        note_launches(1);
+    }
+    BG_CUDA(cudaGetLastError());
+    int32_t a[8];
+    BG_CUDA(cudaMemcpyAsync(a, ar.acc, 6 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    BG_CUDA(cudaStreamSynchronize(st));
+    const int64_t nvalid = a[4];
+    s->info.n_valid = nvalid;
+    if (a[5] != 0) {
+        set_error("a valid sounding lies outside (-2^30, 2^30) cm");
+        return BG_ERR_INVALID_ARG;
+    }
+    if (nvalid == 0) return BG_OK;
+
+    const int64_t W = (int64_t)a[2] - a[0] + 1, H = (int64_t)a[3] - a[1] + 1;
+    const double rho = (double)nvalid / ((double)W * (double)H);
+    int64_t cs = (int64_t)std::ceil(std::sqrt(2.0 / rho));
+    if (cs < 1) cs = 1;
+    if (cs > kCoordLimit) cs = kCoordLimit;
+    int64_t ncx = 0, ncy = 0, nb = 0, nch = 0, sat_rows = kSatRows;
+    for (;;) {
+        ncx = (W + cs - 1) / cs;
+        ncy = (H + cs - 1) / cs;
+        sat_rows = std::max<int64_t>(kSatRows, (ncy + 65534) / 65535);
+        nch = (ncy + sat_rows - 1) / sat_rows;
+        nb = (ncx * ncy + kScanTile - 1) / kScanTile;
+        if (ncx * ncy <= ar.cells_max && (ncx + 1) * (ncy + 1) <= ar.sat_max &&
+            nb + 1 <= ar.bsum_max && nch * (ncx + 1) <= ar.csum_max)
+            break;
+        cs = cs + cs / 4 + 1;
+    }
+    const int64_t ncells = ncx * ncy;
+    s->info.bbox_x0_cm = a[0];
+    s->info.bbox_y0_cm = a[1];
+    s->info.bbox_x1_cm = a[2];
+    s->info.bbox_y1_cm = a[3];
+    s->info.cell_cm = (int32_t)cs;
+    s->info.ncx = (int32_t)ncx;
+    s->info.ncy = (int32_t)ncy;
+
+    const CellGeom g{a[0], a[1], (int32_t)cs, (int32_t)ncx, (int32_t)ncy};
+    BG_CUDA(cudaMemsetAsync(ar.count, 0, (size_t)ncells * 4, st));
+    k_cell_hist<<<grid_for(n, kThreads * 4, 152 * 16), kThreads, 0, st>>>(ar.orig, n, g, ar.count);
+    k_scan_reduce<<<(unsigned)nb, kThreads, 0, st>>>(ar.count, ncells, ar.bsum);
+    k_scan_blocksums<<<1, kThreads, 0, st>>>(ar.bsum, (int)nb, ar.cell_start + ncells);
+    k_scan_apply<<<(unsigned)nb, kThreads, 0, st>>>(ar.count, ncells, ar.bsum, ar.cell_start,
+                                                    ar.count);
+    k_scatter<<<grid_for(n, kThreads * 4, 152 * 16), kThreads, 0, st>>>(ar.orig, n, g, ar.count,
+                                                                        ar.rec);
+    const dim3 sg((unsigned)((ncx + 1 + 255) / 256), (unsigned)nch);
+    k_sat_chunk<<<sg, 256, 0, st>>>(ar.cell_start, (int)ncx, (int)ncy, (int)sat_rows, ar.csum);
+    k_sat_chunkscan<<<(unsigned)((ncx + 1 + 255) / 256), 256, 0, st>>>(ar.csum, (int)ncx, (int)nch);
+    k_sat_apply<<<sg, 256, 0, st>>>(ar.cell_start, ar.csum, (int)ncx, (int)ncy, (int)sat_rows,
+                                    ar.sat);
+    note_launches(8);
+    BG_CUDA(cudaGetLastError());
+
+    s->h.rec = ar.rec;
+    s->h.cell_start = ar.cell_start;
+    s->h.sat = ar.sat;
+    s->h.hx0 = a[0];
+    s->h.hy0 = a[1];
+    s->h.cs = (int32_t)cs;
+    s->h.inv_cs = 1.0f / (float)cs;
+    s->h.ncx = (int32_t)ncx;
+    s->h.ncy = (int32_t)ncy;
+    s->h.n_valid = (int32_t)nvalid;
+    return BG_OK;
+}
+
 }  // namespace bg

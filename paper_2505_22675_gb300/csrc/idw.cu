@@ -140,4 +140,17 @@ bg_status launch_idw(const bg_soundings_s* s, const GridView& g, int k, float po
     return rc;
 }
 
+bg_status launch_idw_with_flag(const bg_soundings_s* s, const GridView& g, int k, float power,
+                               float* depth, int32_t* nbr, int* d_flag, cudaStream_t st) {
+    HashView h = s->h;
+    const int K = k <= 4 ? 4 : k <= 8 ? 8 : k <= 16 ? 16 : 32;
+    h.r0 = start_halfwidth(s, K);
+    switch (K) {
+        case 4: return launch_k<4>(h, g, k, power, depth, nbr, d_flag, st);
+        case 8: return launch_k<8>(h, g, k, power, depth, nbr, d_flag, st);
+        case 16: return launch_k<16>(h, g, k, power, depth, nbr, d_flag, st);
+        default: return launch_k<32>(h, g, k, power, depth, nbr, d_flag, st);
+    }
+}
+
 }  // namespace bg
