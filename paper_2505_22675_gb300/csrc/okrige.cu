@@ -44,12 +44,14 @@ struct Geo {
     static constexpr int G = K / kR;                      // threads per system
     static constexpr int SYS = 32 / G;                    // systems per warp
     static constexpr int LEN = G * kR * (kR + 1) / 2;     // register floats of L
-    static constexpr int ROW = K + 1;                     // smem row stride of A
-    // per-system smem floats, padded to G (mod 32) so that the systems of a
-    // warp read distinct banks
-    static constexpr int MAT = K * ROW + ((G - (K * ROW) % 32) + 32) % 32;
-    static constexpr int TAB = K + 1;                     // neighbour table stride
-    static constexpr int WARP_FLOATS = SYS * (MAT + 4 * TAB);
+    static constexpr int ROW = K + 1;                     // smem row stride (bank = row + col)
+    static constexpr int TAB = K + 1;                     // neighbour table length
+    // per system: one K x (K+1) matrix (lower = fixed-point A, upper = factor
+    // transposed) and three neighbour tables; the stride is = G (mod 32) so
+    // that the G-thread groups of a warp cover all 32 banks
+    static constexpr int RAW = K * ROW + 3 * TAB;
+    static constexpr int SYS_FLOATS = RAW + ((G - RAW % 32) + 32) % 32;
+    static constexpr int WARP_FLOATS = SYS * SYS_FLOATS;
     static __host__ __device__ constexpr int off(int s) { return G * s * (s + 1) / 2; }
 };
 
@@ -68,6 +70,20 @@ __device__ __forceinline__ float gamma_cm(const OkParams& p, int dx, int dy, flo
     const float fx = (float)dx, fy = (float)dy;
     const float d2 = fmaf(fx, fx, fy * fy);
     return variogram(p, d2 * rsqrtf(d2) * 0.01f);
+}
+
+// gamma between two distinct soundings from float offsets in cm (exact
+// integers below 2^24); zero separation gives the nugget c0 (the h -> 0+
+// limit) without a branch: t = min(h/a, 1) makes the spherical model's
+// polynomial equal the sill beyond the range
+__device__ __forceinline__ float gamma_pair_f(const OkParams& p, float dx, float dy) {
+    const float d2 = fmaf(dx, dx, dy * dy);
+    const float h_cm = d2 * rsqrtf(d2 + 1e-30f);
+    if (p.model == BG_VARIOGRAM_SPHERICAL) {
+        const float t = fminf(h_cm * p.inv_a * 0.01f, 1.0f);
+        return fmaf(p.c * t, fmaf(-0.5f * t, t, 1.5f), p.c0);
+    }
+    return fmaf(p.c, 1.0f - __expf(-h_cm * p.inv_a * 0.01f), p.c0);
 }
 
 // ------------------------------------------------------------ k-NN -> ids
@@ -128,21 +144,13 @@ __global__ void __launch_bounds__(128) k_knn_ids_wide(HashView h, GridView g, in
 
 // ---------------------------------------------------------------- solve
 
-// error-free transformation: a + b = s + e exactly
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-    s = a + b;
-    const float bb = s - a;
-    e = (a - (s - bb)) + (b - bb);
-}
+__host__ __device__ constexpr int tri(int r) { return r * (r + 1) / 2; }
 
-// The factor and solve sweeps below are written as one function per column
-// j, expanded over j = 0..K-1 with an integer_sequence, so that every index
-// into the register arrays is a compile-time constant (a plain nested
-// #pragma unroll over the triangle is too large for the unroller, which then
-// leaves the arrays in local memory).
-
-// Cholesky column j: scale by the pivot, then update the trailing rows with
-// column j broadcast within the group.
+// Cholesky column j of the register-held lower triangle: scale by the pivot,
+// then update the trailing rows with column j broadcast within the group.
+// Expanded over j with an integer_sequence so every register index is a
+// compile-time constant (a nested #pragma unroll over the whole triangle is
+// beyond the unroller and would leave L in local memory).
 template <int K, int J>
 __device__ __forceinline__ void chol_column(float (&L)[Geo<K>::LEN], float (&dinv)[kR], int t,
                                             int gbase) {
@@ -177,7 +185,7 @@ __device__ __forceinline__ void chol_factor(float (&L)[Geo<K>::LEN], float (&din
     (chol_column<K, J>(L, dinv, t, gbase), ...);
 }
 
-// forward sweep step j of L y = v
+// forward sweep step j of L y = v (L rows in registers)
 template <int K, int J>
 __device__ __forceinline__ void fwd_step(const float (&L)[Geo<K>::LEN], const float (&dinv)[kR],
                                          float (&v)[kR], int t, int gbase) {
@@ -191,37 +199,36 @@ __device__ __forceinline__ void fwd_step(const float (&L)[Geo<K>::LEN], const fl
         if (G * (s + 1) - 1 > J && G * s + t > J) v[s] = fmaf(-L[Gm::off(s) + J], yj, v[s]);
 }
 
-// transposed sweep step for column j = K-1-I of L^T x = y
+// transposed sweep for column j = K-1-I of L^T x = y: the owner of row j
+// finishes x_j and broadcasts it; rows r < j subtract L[j][r] x_j, read from
+// the transposed copy of the factor at (r, j) in shared memory
 template <int K, int I>
-__device__ __forceinline__ void bwd_step(const float (&L)[Geo<K>::LEN], const float (&dinv)[kR],
-                                         float (&v)[kR], int t) {
+__device__ __forceinline__ void bwd_step(const float* Lt, const float (&dinv)[kR], float (&v)[kR],
+                                         int t, int gbase) {
     using Gm = Geo<K>;
     constexpr int G = Gm::G;
     constexpr int J = K - 1 - I;
     constexpr int SJ = J / G;
-    float q = 0.0f;
+    if (t == J % G) v[SJ] *= dinv[SJ];
+    const float xj = __shfl_sync(kFull, v[SJ], gbase + J % G);
 #pragma unroll
     for (int s = 0; s < kR; ++s)
-        if (G * (s + 1) - 1 > J && G * s + t > J) q = fmaf(L[Gm::off(s) + J], v[s], q);
-#pragma unroll
-    for (int o = 1; o < G; o <<= 1) q += __shfl_xor_sync(kFull, q, o);
-    if (t == J % G) v[SJ] = (v[SJ] - q) * dinv[SJ];
+        if (G * s < J && G * s + t < J) v[s] = fmaf(-Lt[(G * s + t) * Gm::ROW + J], xj, v[s]);
 }
 
-// L L^T v = v in place for the system of this thread's group.
 template <int K, int... J>
-__device__ __forceinline__ void chol_solve_seq(const float (&L)[Geo<K>::LEN],
+__device__ __forceinline__ void chol_solve_seq(const float (&L)[Geo<K>::LEN], const float* Lt,
                                                const float (&dinv)[kR], float (&v)[kR], int t,
                                                int gbase, std::integer_sequence<int, J...>) {
     (fwd_step<K, J>(L, dinv, v, t, gbase), ...);
-    (bwd_step<K, J>(L, dinv, v, t), ...);
+    (bwd_step<K, J>(Lt, dinv, v, t, gbase), ...);
 }
 
-template <int K>
-__device__ __forceinline__ void chol_solve(const float (&L)[Geo<K>::LEN], const float (&dinv)[kR],
-                                           float (&v)[kR], int t, int gbase) {
-    chol_solve_seq<K>(L, dinv, v, t, gbase, std::make_integer_sequence<int, K>{});
-}
+// 2^e as a float (|e| <= 126)
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((127 + e) << 23); }
+
+// exponent e with 2^(e-1) <= v < 2^e for finite v > 0
+__device__ __forceinline__ int exp_above(float v) { return ((__float_as_int(v) >> 23) & 0xff) - 126; }
 
 template <int K>
 __global__ void __launch_bounds__(kSolveWarps * 32) k_okrige_solve(
@@ -229,15 +236,16 @@ __global__ void __launch_bounds__(kSolveWarps * 32) k_okrige_solve(
     const int32_t* __restrict__ ids, float* __restrict__ depth, float* __restrict__ var) {
     using Gm = Geo<K>;
     constexpr int G = Gm::G;
+    constexpr int ROW = Gm::ROW;
     __shared__ float smem[kSolveWarps * Gm::WARP_FLOATS];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int grp = lane / G, t = lane % G, gbase = grp * G;
-    float* A0 = smem + warp * Gm::WARP_FLOATS + grp * Gm::MAT;
-    float* tabs = smem + warp * Gm::WARP_FLOATS + Gm::SYS * Gm::MAT;
-    int* tx = reinterpret_cast<int*>(tabs) + grp * Gm::TAB;                 // x of neighbour n
-    int* ty = reinterpret_cast<int*>(tabs) + (Gm::SYS + grp) * Gm::TAB;     // y of neighbour n
-    float* tz = tabs + (2 * Gm::SYS + grp) * Gm::TAB;                       // depth of neighbour 0
-    float* tg = tabs + (3 * Gm::SYS + grp) * Gm::TAB;                       // Gamma(row r, 0)
+    float* sysmem = smem + warp * Gm::WARP_FLOATS + grp * Gm::SYS_FLOATS;
+    int* Aq = reinterpret_cast<int*>(sysmem);      // lower triangle: fixed-point A
+    float* Lt = sysmem;                             // strict upper triangle: L transposed
+    float* fx = sysmem + K * ROW;                   // x of neighbour n minus x of neighbour 0 (cm)
+    float* fy = fx + Gm::TAB;                       // y likewise
+    float* tg = fy + Gm::TAB;                       // Gamma(neighbour of row r, neighbour 0)
     const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << gbase);
 
     for (int round = 0; round < kRounds; ++round) {
@@ -258,116 +266,134 @@ __global__ void __launch_bounds__(kSolveWarps * 32) k_okrige_solve(
             cnt += __popc(__ballot_sync(kFull, nid[s] >= 0) & gmask);
         }
         const int id0 = live ? __ldg(my) : -1;
-        const int ke = (id0 >= 0) ? 1 + (int)cnt : 0;  // 0: no output (empty or past the end)
+        const int ke = (id0 >= 0) ? 1 + (int)cnt : 0;  // 0: no output (no data, or past the end)
         const int qx = g.x0 + (int)(node % g.nx) * g.cell + g.cell / 2;
         const int qy = g.y0 + (int)(node / g.nx) * g.cell + g.cell / 2;
 
-        // gather the neighbours' records into the system's table
-        float zr[kR];
-        if (t == 0) {
-            int4 r0 = make_int4(0, 0, 0, 0);
-            if (id0 >= 0) r0 = __ldg(h.orig + id0);
-            tx[0] = r0.x;
-            ty[0] = r0.y;
-            tz[0] = __int_as_float(r0.z);
-        }
+        // gather the neighbours' records; offsets from neighbour 0 as exact floats
+        int4 r0 = make_int4(0, 0, 0, 0);
+        if (id0 >= 0) r0 = __ldg(h.orig + id0);
+        const float z0 = __int_as_float(r0.z);
+        const float g00 = gamma_cm(p, r0.x - qx, r0.y - qy, 0.0f);
+        float zr[kR], gr0[kR], g0r[kR];  // depth; Gamma(row's neighbour, nbr 0); gamma(node, row's nbr)
+        float gmax = 0.0f;
 #pragma unroll
         for (int s = 0; s < kR; ++s) {
             int4 rr = make_int4(0, 0, 0, 0);
-            if (nid[s] >= 0) rr = __ldg(h.orig + nid[s]);
-            const int n = 1 + G * s + t;  // <= K = TAB - 1
-            tx[n] = rr.x;
-            ty[n] = rr.y;
+            const bool real = nid[s] >= 0;
+            if (real) rr = __ldg(h.orig + nid[s]);
+            const int r = G * s + t;
+            const float ox = (float)(rr.x - r0.x), oy = (float)(rr.y - r0.y);
+            fx[r + 1] = ox;
+            fy[r + 1] = oy;
             zr[s] = __int_as_float(rr.z);
+            gr0[s] = real ? gamma_pair_f(p, ox, oy) : 0.0f;
+            g0r[s] = real ? gamma_cm(p, rr.x - qx, rr.y - qy, 0.0f) : 0.0f;
+            tg[r] = gr0[s];
+            gmax = fmaxf(gmax, gr0[s]);
         }
-        __syncwarp();
-        const int x0 = tx[0], y0 = ty[0];
-        const float z0 = tz[0];
-        const float g00 = gamma_cm(p, x0 - qx, y0 - qy, 0.0f);
-        float gr0[kR], g0r[kR];  // Gamma(neighbour of row, neighbour 0), gamma(node, that neighbour)
 #pragma unroll
-        for (int s = 0; s < kR; ++s) {
-            const int n = 1 + G * s + t;
-            const bool real = n < ke;
-            gr0[s] = real ? gamma_cm(p, tx[n] - x0, ty[n] - y0, p.c0) : 0.0f;
-            g0r[s] = real ? gamma_cm(p, tx[n] - qx, ty[n] - qy, 0.0f) : 0.0f;
-            tg[G * s + t] = gr0[s];
+        for (int o = 1; o < G; o <<= 1) gmax = fmaxf(gmax, __shfl_xor_sync(kFull, gmax, o));
+        // A is SPD, so |A[r][c]| <= its largest diagonal entry max(1, 2 max Gamma_r0);
+        // fixed point with 30 bits below that bound
+        const int ea = 30 - exp_above(fmaxf(1.0f, 2.0f * gmax));
+        const float sa = pow2f(ea), isa = pow2f(-ea);
+        __syncwarp();
+
+        // assemble the lower triangle once per entry (the group's threads take
+        // the columns c = t, t + G, ... of each row), straight into fixed point
+        for (int r = 0; r < K; ++r) {
+            const bool row = r + 1 < ke;
+            const float xr = fx[r + 1], yr = fy[r + 1], grr = tg[r];
+            for (int c = t; c <= r; c += G) {
+                float v;
+                if (c == r)
+                    v = row ? 2.0f * grr : 1.0f;
+                else
+                    v = (row && c + 1 < ke)
+                            ? (grr + tg[c]) - gamma_pair_f(p, xr - fx[c + 1], yr - fy[c + 1])
+                            : 0.0f;
+                Aq[r * ROW + c] = __float2int_rn(v * sa);
+            }
         }
         __syncwarp();
 
-        // assemble: lower triangle into registers, the full symmetric matrix into smem
+        // my rows into registers (zero above the diagonal)
         float L[Gm::LEN];
         float b[kR];
 #pragma unroll
         for (int s = 0; s < kR; ++s) {
             const int r = G * s + t;
-            const bool row = r + 1 < ke;
-            const int xr = tx[r + 1], yr = ty[r + 1];
-            b[s] = row ? (gr0[s] + g00) - g0r[s] : 0.0f;
+            b[s] = (r + 1 < ke) ? (gr0[s] + g00) - g0r[s] : 0.0f;
 #pragma unroll
             for (int c = 0; c < G * (s + 1); ++c) {
-                float v;
-                if (c < r) {
-                    v = (row && c + 1 < ke)
-                            ? (gr0[s] + tg[c]) - gamma_cm(p, xr - tx[c + 1], yr - ty[c + 1], p.c0)
-                            : 0.0f;
-                } else if (c == r) {
-                    v = row ? 2.0f * gr0[s] : 1.0f;
-                } else {
-                    v = 0.0f;  // unused upper part
-                }
-                L[Gm::off(s) + c] = v;
-                if (c <= r) {
-                    A0[r * Gm::ROW + c] = v;
-                    A0[c * Gm::ROW + r] = v;
-                }
+                const int q = Aq[c <= r ? r * ROW + c : 0];
+                L[Gm::off(s) + c] = c <= r ? (float)q * isa : 0.0f;
             }
         }
 
-        // Cholesky in registers
+        // factor in registers; L transposed into the upper triangle for the
+        // back sweeps (row r, column c < r goes to (c, r))
         float dinv[kR];
 #pragma unroll
         for (int s = 0; s < kR; ++s) dinv[s] = 1.0f;
         chol_factor<K>(L, dinv, t, gbase, std::make_integer_sequence<int, K>{});
-        __syncwarp();
-
-        float x[kR];
-#pragma unroll
-        for (int s = 0; s < kR; ++s) x[s] = b[s];
-        chol_solve<K>(L, dinv, x, t, gbase);
-
-        // residual b - A x against the original A, as an FP32 double-word:
-        // exact products (FMA error term) and error-free running sums
-        float rh[kR], rl[kR];
 #pragma unroll
         for (int s = 0; s < kR; ++s) {
-            rh[s] = b[s];
-            rl[s] = 0.0f;
+            const int r = G * s + t;
+#pragma unroll
+            for (int c = 0; c < G * (s + 1); ++c)
+                if (c < r) Lt[c * ROW + r] = L[Gm::off(s) + c];
         }
+        __syncwarp();
+
+        // solve, one refinement step, solve again. The residual b - A' x' is
+        // exact: x' is x rounded to 24-bit fixed point (representable in FP32),
+        // A' the 30-bit copy, and the sum of the 2^54-bounded products is
+        // accumulated in 64-bit integers without rounding.
+        float v[kR], x[kR];
 #pragma unroll
-        for (int sc = 0; sc < kR; ++sc) {
-#pragma unroll 2
-            for (int tc = 0; tc < G; ++tc) {
-                const int c = G * sc + tc;
-                const float xc = __shfl_sync(kFull, x[sc], gbase + tc);
+        for (int s = 0; s < kR; ++s) v[s] = b[s];
+#pragma unroll 1
+        for (int pass = 0; pass < 2; ++pass) {
+            chol_solve_seq<K>(L, Lt, dinv, v, t, gbase, std::make_integer_sequence<int, K>{});
+            if (pass == 1) {
 #pragma unroll
-                for (int s = 0; s < kR; ++s) {
-                    const float a = A0[(G * s + t) * Gm::ROW + c];
-                    const float ph = -a * xc;
-                    const float pl = fmaf(-a, xc, -ph);
-                    float sh, se;
-                    two_sum(rh[s], ph, sh, se);
-                    rh[s] = sh;
-                    rl[s] += se + pl;
+                for (int s = 0; s < kR; ++s) x[s] += v[s];
+                break;
+            }
+            float xmax = 0.0f;
+#pragma unroll
+            for (int s = 0; s < kR; ++s) xmax = fmaxf(xmax, fabsf(v[s]));
+#pragma unroll
+            for (int o = 1; o < G; o <<= 1) xmax = fmaxf(xmax, __shfl_xor_sync(kFull, xmax, o));
+            const int ex = xmax > 0.0f ? 24 - exp_above(xmax) : 0;
+            const float sx = pow2f(ex), isx = pow2f(-ex);
+            int xq[kR];
+            long long acc[kR];
+#pragma unroll
+            for (int s = 0; s < kR; ++s) {
+                xq[s] = __float2int_rn(v[s] * sx);
+                x[s] = (float)xq[s] * isx;
+                acc[s] = __float2ll_rn((b[s] * sa) * sx);
+            }
+#pragma unroll
+            for (int sc = 0; sc < kR; ++sc) {
+#pragma unroll 4
+                for (int tc = 0; tc < G; ++tc) {
+                    const int c = G * sc + tc;
+                    const int xc = __shfl_sync(kFull, xq[sc], gbase + tc);
+#pragma unroll
+                    for (int s = 0; s < kR; ++s) {
+                        const int r = G * s + t;
+                        const int a = Aq[max(r, c) * ROW + min(r, c)];
+                        acc[s] -= (long long)a * (long long)xc;
+                    }
                 }
             }
+#pragma unroll
+            for (int s = 0; s < kR; ++s) v[s] = ((float)acc[s] * isa) * isx;
         }
-        float dx[kR];
-#pragma unroll
-        for (int s = 0; s < kR; ++s) dx[s] = rh[s] + rl[s];
-        chol_solve<K>(L, dinv, dx, t, gbase);
-#pragma unroll
-        for (int s = 0; s < kR; ++s) x[s] += dx[s];
 
         // weights and outputs; the weight sum closes in FP64
         float ps = 0.0f, pz = 0.0f, pv = 0.0f;
