@@ -215,6 +215,107 @@ __device__ __forceinline__ int knn_scan(const HashView& h, int qx, int qy, const
     return keff;
 }
 
+// ---------------------------------------------------------------------------
+// Packed-key search with the K best kept in a per-thread max-heap in shared
+// memory (element i of a thread's heap at hp[i * S], S = threads per block,
+// so the warp's accesses never share a bank whatever the heap positions).
+// Inserting into a full heap replaces the root and sifts it down: O(log K)
+// instead of the O(K) compare-select chain of a sorted register array, which
+// SIMT pays for whenever any lane of the warp inserts.
+
+template <int S>
+__device__ __forceinline__ void heap_sift_down(uint64_t* hp, int i, int n, uint64_t v) {
+    for (;;) {
+        const int l = 2 * i + 1;
+        if (l >= n) break;
+        int m = l;
+        uint64_t km = hp[l * S];
+        if (l + 1 < n) {
+            const uint64_t kr = hp[(l + 1) * S];
+            if (kr > km) {
+                m = l + 1;
+                km = kr;
+            }
+        }
+        if (km < v) break;
+        hp[i * S] = km;
+        i = m;
+    }
+    hp[i * S] = v;
+}
+
+template <int S>
+__device__ __forceinline__ void heap_build(uint64_t* hp, int n) {
+    for (int i = n / 2 - 1; i >= 0; --i) heap_sift_down<S>(hp, i, n, hp[i * S]);
+}
+
+// Phase 2 with the heap. On return hp[0 .. keff) holds the neighbours' packed
+// keys in ascending order; returns keff (<= K). Requires packed_fits(tau0).
+template <int K, int S>
+__device__ __forceinline__ int knn_scan_heap(const HashView& h, int qx, int qy, const Bound& b,
+                                             uint64_t* hp) {
+    const int bits = h.idx_bits;
+    const int64_t tau0 = b.tau0;
+    const uint64_t sentinel = (uint64_t)(tau0 + 1) << bits;
+    uint64_t root = sentinel;  // the K-th best key once the heap is full
+    int cnt = 0;
+    int64_t tau = tau0;
+    int up = b.cy, dn = b.cy - 1;
+    const int64_t xmin = h.hx0;
+    const int64_t xmax = (int64_t)h.hx0 + (int64_t)h.ncx * h.cs - 1;
+    for (;;) {
+        int64_t dyu = LLONG_MAX, dyd = LLONG_MAX;
+        if (up < h.ncy) {
+            const int64_t ylo = (int64_t)h.hy0 + (int64_t)up * h.cs, yhi = ylo + h.cs - 1;
+            dyu = qy < ylo ? ylo - qy : (qy > yhi ? qy - yhi : 0);
+        }
+        if (dn >= 0) {
+            const int64_t ylo = (int64_t)h.hy0 + (int64_t)dn * h.cs, yhi = ylo + h.cs - 1;
+            dyd = qy < ylo ? ylo - qy : (qy > yhi ? qy - yhi : 0);
+        }
+        const bool take_up = dyu <= dyd;
+        const int64_t dy = take_up ? dyu : dyd;
+        if (dy == LLONG_MAX || dy * dy > tau) break;
+        const int row = take_up ? up++ : dn--;
+        const int64_t dxm = isqrt_ub(tau - dy * dy);
+        const int64_t xa = max((int64_t)qx - dxm, xmin), xb = min((int64_t)qx + dxm, xmax);
+        if (xa > xb) continue;
+        const int ca = cell_of(h, xa - h.hx0), cb = cell_of(h, xb - h.hx0);
+        const int rowbase = row * h.ncx;
+        const int s = __ldg(h.cell_start + rowbase + ca);
+        const int e = __ldg(h.cell_start + rowbase + cb + 1);
+        const uint64_t utau = (uint64_t)tau;
+        for (int p = s; p < e; ++p) {
+            const int4 v = __ldg(h.rec + p);
+            const int ddx = v.x - qx, ddy = v.y - qy;
+            const uint64_t d2 = (uint64_t)((long long)ddx * ddx + (long long)ddy * ddy);
+            if (d2 > utau) continue;
+            const uint64_t c = (d2 << bits) | (uint32_t)v.w;
+            if (c < root) {
+                if (cnt < K) {
+                    hp[cnt * S] = c;
+                    if (++cnt == K) {
+                        heap_build<S>(hp, K);
+                        root = hp[0];
+                    }
+                } else {
+                    heap_sift_down<S>(hp, 0, K, c);
+                    root = hp[0];
+                }
+            }
+        }
+        tau = min(tau, (int64_t)(root >> bits));
+    }
+    // heapsort into ascending order
+    if (cnt < K) heap_build<S>(hp, cnt);
+    for (int e = cnt - 1; e > 0; --e) {
+        const uint64_t v = hp[e * S];
+        hp[e * S] = hp[0];
+        heap_sift_down<S>(hp, 0, e, v);
+    }
+    return cnt;
+}
+
 // Grid node (i, j) owned by this thread inside the 16 x 8 node patch (px, py).
 // Each warp covers 8 x 4 nodes, so a warp's nodes are spatially compact.
 struct NodeIdx {

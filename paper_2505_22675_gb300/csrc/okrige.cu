@@ -91,42 +91,49 @@ __device__ __forceinline__ float gamma_pair_f(const OkParams& p, float dx, float
 template <int K, bool kWide>
 __device__ __forceinline__ void knn_ids_node(const HashView& h, const GridView& g, int k,
                                              int64_t node0, int32_t* __restrict__ ids,
-                                             int* __restrict__ flag, NodeIdx nd, int j1) {
+                                             int* __restrict__ flag, NodeIdx nd, int j1,
+                                             uint64_t* hp) {
     if (nd.i >= g.nx || nd.j >= j1) return;
     const int64_t node = (int64_t)nd.j * g.nx + nd.i;
     const int qx = g.x0 + nd.i * g.cell + g.cell / 2;
     const int qy = g.y0 + nd.j * g.cell + g.cell / 2;
-    uint64_t d2[K];
-    int id[K];
-    int keff = 0;
-    if (h.n_valid > 0) {
-        const Bound b = knn_bound<K>(h, qx, qy);
-        const bool fits = packed_fits(h, b.tau0);
-        if (kWide) {
-            if (fits) return;
-        } else if (!fits) {
+    int32_t* o = ids + (node - node0) * k;
+    if (h.n_valid == 0) {
+        if (!kWide)
+            for (int i = 0; i < k; ++i) o[i] = -1;
+        return;
+    }
+    const Bound b = knn_bound<K>(h, qx, qy);
+    const bool fits = packed_fits(h, b.tau0);
+    if constexpr (kWide) {
+        if (fits) return;
+        uint64_t d2[K];
+        int id[K];
+        const int keff = knn_scan<K, true>(h, qx, qy, b, d2, id);
+#pragma unroll
+        for (int i = 0; i < K; ++i)
+            if (i < k) o[i] = i < keff ? id[i] : -1;
+    } else {
+        if (!fits) {
             *flag = 1;
             return;
         }
-        keff = knn_scan<K, kWide>(h, qx, qy, b, d2, id);
-    } else if (kWide) {
-        return;
+        const int keff = knn_scan_heap<K, 128>(h, qx, qy, b, hp);
+        const uint64_t mask = (1ull << h.idx_bits) - 1;
+        for (int i = 0; i < k; ++i) o[i] = i < keff ? (int)(hp[i * 128] & mask) : -1;
     }
-    int32_t* o = ids + (node - node0) * k;
-#pragma unroll
-    for (int i = 0; i < K; ++i)
-        if (i < k) o[i] = i < keff ? id[i] : -1;
 }
 
 // grid rows [j0, j1); j0 is a multiple of 8
 template <int K>
 __global__ void __launch_bounds__(128) k_knn_ids(HashView h, GridView g, int k, int j0, int j1,
                                                  int32_t* __restrict__ ids, int* __restrict__ flag) {
+    __shared__ uint64_t heap[K * 128];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int gx = (g.nx + 15) / 16;
     const int px = blockIdx.x % gx, py = j0 / 8 + blockIdx.x / gx;
     knn_ids_node<K, false>(h, g, k, (int64_t)j0 * g.nx, ids, flag,
-                           patch_node(px, py, warp, lane), j1);
+                           patch_node(px, py, warp, lane), j1, heap + threadIdx.x);
 }
 
 template <int K>
@@ -139,7 +146,8 @@ __global__ void __launch_bounds__(128) k_knn_ids_wide(HashView h, GridView g, in
     const int64_t nb = (int64_t)gx * ((j1 - j0 + 7) / 8);
     for (int64_t b = blockIdx.x; b < nb; b += gridDim.x)
         knn_ids_node<K, true>(h, g, k, (int64_t)j0 * g.nx, ids, flag,
-                              patch_node((int)(b % gx), j0 / 8 + (int)(b / gx), warp, lane), j1);
+                              patch_node((int)(b % gx), j0 / 8 + (int)(b / gx), warp, lane), j1,
+                              nullptr);
 }
 
 // ---------------------------------------------------------------- solve
