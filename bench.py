@@ -169,6 +169,86 @@ def cpu_baseline(w, target_s: float = 15.0):
 
 # ------------------------------------------------------------------- main
 
+# ------------------------------------------------------------------ serving
+
+def serving_pool(count: int, seed: int = 3):
+    """Tiles shaped like the batched/serving workload (lognormal N with median
+    20k in [1k, 200k], grid side 64-1024 at 1-4 m, IDW k=16 / kriging k=32)."""
+    return synth.batched_tiles(seed=seed, count=count)
+
+
+def _percentile(a, q):
+    return float(np.percentile(np.asarray(a, dtype=np.float64), q)) if len(a) else None
+
+
+def serving_measure(bg, torch, ctx, pool, rate, n_tiles, seed):
+    """Poisson arrivals at `rate` tiles/s: the serving loop (bg_submit) against
+    one synchronous call sequence per tile in arrival order (the plain path).
+    Latency = arrival -> grids in host memory. Returns a dict of p50/p99 ms
+    and nodes/s for both."""
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1.0 / rate, n_tiles)
+    arrivals = np.cumsum(gaps) - gaps[0]
+    pick = rng.integers(0, len(pool), n_tiles)
+    vgm = bg.variogram(*VGM)
+
+    def spec(w):
+        g = w.grid
+        return (g.x0_cm, g.y0_cm, g.cell_cm, g.nx, g.ny)
+
+    # serving path
+    tickets = []
+    t0 = time.perf_counter()
+    for i in range(n_tiles):
+        target = t0 + arrivals[i]
+        while True:
+            dt = target - time.perf_counter()
+            if dt <= 0:
+                break
+            if dt > 2e-3:
+                time.sleep(dt - 1e-3)
+        w, m = pool[pick[i]]
+        d = np.empty(w.grid.m, np.float32)
+        v = np.empty(w.grid.m, np.float32) if m == 1 else None
+        tickets.append(bg.submit(ctx, w.x_cm, w.y_cm, w.z_m, spec(w), m, 16 if m == 0 else 32, d, v,
+                                 power=IDW_P, vgm=vgm))
+    res = [bg.wait(ctx, t, 600_000) for t in tickets]
+    lat = [(r.t_done_us - r.t_submit_us) / 1e3 for r in res]
+    span = (max(r.t_done_us for r in res) - min(r.t_submit_us for r in res)) / 1e6
+    nodes = sum(r.nodes for r in res)
+    serve = {"p50_ms": _percentile(lat, 50), "p99_ms": _percentile(lat, 99),
+             "nodes_per_s": nodes / span, "errors": sum(1 for r in res if r.status != 0)}
+
+    # plain path: one synchronous call sequence per tile, first come first served
+    dev = torch.device("cuda", torch.cuda.current_device())
+    lat = []
+    t0 = time.perf_counter()
+    for i in range(n_tiles):
+        target = t0 + arrivals[i]
+        while time.perf_counter() < target:
+            pass
+        w, m = pool[pick[i]]
+        g = w.grid
+        grid = bg.grid_create(ctx, *spec(w))
+        s = bg.soundings_upload(ctx, w.x_cm, w.y_cm, w.z_m)
+        d = torch.empty(g.m, device=dev)
+        if m == 0:
+            bg.interp_idw(s, grid, 16, IDW_P, d)
+            d.cpu()
+        else:
+            v = torch.empty(g.m, device=dev)
+            bg.interp_okrige(s, grid, 32, vgm, d, v)
+            d.cpu()
+            v.cpu()
+        bg.soundings_destroy(s)
+        bg.grid_destroy(grid)
+        lat.append((time.perf_counter() - target) * 1e3)
+    span = time.perf_counter() - t0
+    plain = {"p50_ms": _percentile(lat, 50), "p99_ms": _percentile(lat, 99),
+             "nodes_per_s": sum(pool[j][0].grid.m for j in pick) / span}
+    return {"rate_per_s": rate, "tiles": n_tiles, "serving": serve, "plain": plain}
+
+
 def workload(args):
     if args.small:
         return synth.swath(seed=2, lines=2, pings=2000, beams=256)
@@ -359,6 +439,24 @@ def bench_ours(args):
                     "d2h_bytes_per_step": int(12 * m), "ms_per_step": e2e_ms},
             "gpu_launches": int(launches), "clocks": clocks, "nan_outputs": bad,
         }
+        if not args.no_serving:
+            pool = serving_pool(args.serving_pool)
+            rates = [50, 200, 500, 1000, 2000] if args.serving else [500, 1000]
+            n_t = args.serving_tiles if args.serving else 300
+            out["serving"] = {
+                "workload": (f"{len(pool)} distinct tiles drawn with replacement: lognormal N "
+                             "(median 20k, 1k-200k), grid side 64-1024 at 1-4 m, IDW k=16 / "
+                             "kriging k=32 50/50; Poisson arrivals; latency = arrival to grids in "
+                             "host memory; plain = one synchronous call sequence per tile, FIFO"),
+                "hbm_budget_bytes": 40 << 30,
+                "rates": []}
+            sctx = bg.ctx_create(local, 40 << 30)
+            try:
+                for i, r in enumerate(rates):
+                    out["serving"]["rates"].append(
+                        serving_measure(bg, torch, sctx, pool, r, n_t, seed=17 + i))
+            finally:
+                bg.ctx_destroy(sctx)
         if not args.no_cpu_baseline and ws == 1:
             out["cpu_baseline"] = cpu_baseline(w, target_s=args.cpu_seconds)
         print(json.dumps(out), flush=True)
@@ -379,6 +477,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-nodes", type=int, default=256, help="reference arm: nodes per step")
+    ap.add_argument("--serving", action="store_true",
+                    help="full serving sweep: 50-2000 tiles/s, --serving-tiles tiles per rate")
+    ap.add_argument("--serving-tiles", type=int, default=2000)
+    ap.add_argument("--serving-pool", type=int, default=48)
+    ap.add_argument("--no-serving", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         bench_reference(args)

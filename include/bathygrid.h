@@ -151,6 +151,60 @@ bg_status bg_interp_okrige(bg_soundings_t s, bg_grid_t grid, int k, const bg_var
                            float* depth_out, float* var_out, int32_t* nbr_out,
                            void* cuda_stream);
 
+/* ---------------------------------------------------------------- serving */
+
+/* A gridding request for bg_submit. Inputs and outputs are HOST memory; the
+ * caller keeps them valid until the ticket completes. */
+typedef struct bg_request {
+    const int32_t* x_cm;       /* n soundings (host) */
+    const int32_t* y_cm;
+    const float* z_m;          /* NaN = invalid sounding */
+    int64_t n;
+    int32_t x0_cm, y0_cm, cell_cm, nx, ny;   /* output grid, as bg_grid_create */
+    int32_t method;            /* 0 = IDW, 1 = ordinary kriging */
+    int32_t k;                 /* neighbours, [1, 32] */
+    float power;               /* IDW exponent (> 0) */
+    bg_variogram variogram;    /* kriging model */
+    float* depth_out;          /* host, nx*ny, row-major */
+    float* var_out;            /* host, nx*ny kriging variance, or NULL */
+} bg_request;
+
+typedef struct bg_result {
+    int32_t status;            /* bg_status of the request (BG_OK, BG_ERR_CANCELLED, ...) */
+    int64_t nodes;             /* nx*ny */
+    double t_submit_us;        /* context clock (microseconds): bg_submit */
+    double t_start_us;         /* admission: the request's work was issued */
+    double t_done_us;          /* its grids were in depth_out / var_out */
+} bg_result;
+
+/* Queue a request; returns at once with a ticket. Requests are admitted in
+ * arrival order when one of the context's stream slots is free and the
+ * context's HBM budget (bg_ctx_create) covers the request's estimated device
+ * memory; admitted requests run concurrently on the device (continuous
+ * batching). A request whose estimate alone exceeds the budget is refused
+ * with BG_ERR_OOM_BUDGET. Thread-safe. */
+bg_status bg_submit(bg_ctx_t ctx, const bg_request* req, uint64_t* ticket);
+
+/* Never blocks. BG_PENDING while the ticket runs; otherwise BG_OK with *out
+ * filled, and the ticket is released (do not poll it again). Unknown ticket:
+ * BG_ERR_NOT_FOUND. */
+bg_status bg_poll(bg_ctx_t ctx, uint64_t ticket, bg_result* out);
+
+/* As bg_poll, but waits up to timeout_ms (< 0: no limit); BG_ERR_TIMEOUT when
+ * the time runs out (the ticket stays valid). */
+bg_status bg_wait(bg_ctx_t ctx, uint64_t ticket, int timeout_ms, bg_result* out);
+
+/* Cancel a ticket that has not started; it completes with BG_ERR_CANCELLED.
+ * A running ticket cannot be cancelled (BG_ERR_INVALID_ARG). */
+bg_status bg_cancel(bg_ctx_t ctx, uint64_t ticket);
+
+/* Requests waiting, requests on the device, and device bytes reserved by them. */
+bg_status bg_serve_stats(bg_ctx_t ctx, int64_t* queued, int64_t* running, int64_t* reserved_bytes);
+
+/* Stop serving: cancel queued tickets and wait for running ones (also done by
+ * bg_ctx_destroy). */
+bg_status bg_serve_shutdown(bg_ctx_t ctx);
+
 /* ------------------------------------------------- allocation-free IDW */
 
 /* IDW gridding that allocates no device memory, for callers that cannot call

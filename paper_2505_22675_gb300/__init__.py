@@ -16,7 +16,7 @@ from __future__ import annotations
 import ctypes
 
 from . import _capi
-from ._capi import BGError, SoundingsInfo, Variogram, check
+from ._capi import BGError, Request, Result, SoundingsInfo, Variogram, check
 
 SPHERICAL = 0
 EXPONENTIAL = 1
@@ -27,7 +27,8 @@ __all__ = [
     "BGError", "Variogram", "SoundingsInfo", "SPHERICAL", "EXPONENTIAL", "IDW", "OKRIGE",
     "version", "launch_count", "ctx_create", "ctx_destroy", "ctx_device_bytes", "grid_create", "grid_destroy",
     "soundings_upload", "soundings_info", "soundings_destroy", "interp_idw", "interp_okrige",
-    "variogram", "interp_idw_noalloc",
+    "variogram", "interp_idw_noalloc", "submit", "poll", "wait", "cancel", "serve_stats",
+    "serve_shutdown", "Request", "Result",
 ]
 
 
@@ -175,6 +176,73 @@ def interp_idw_noalloc(x_cm, y_cm, z_m, grid_spec, k: int, power: float, depth_o
                                        x0, y0, cell, nx, ny, k, power, _ptr(depth_out),
                                        _ptr(nbr_out), _stream(stream, depth_out)),
           "bg_interp_idw_noalloc")
+
+
+# host arrays of submitted requests, kept alive until their ticket completes
+_inflight = {}
+
+
+def submit(ctx, x_cm, y_cm, z_m, grid_spec, method: int, k: int, depth_out, var_out=None,
+           power: float = 2.0, vgm: Variogram | None = None) -> int:
+    """Queue a gridding request on host arrays; returns its ticket.
+
+    grid_spec = (x0_cm, y0_cm, cell_cm, nx, ny); method IDW (0) or OKRIGE (1).
+    depth_out / var_out are host float32 arrays of nx*ny, written when the
+    ticket completes; all arrays are kept alive here until then.
+    """
+    import numpy as np
+    arrs = [np.ascontiguousarray(a, dtype=d) for a, d in
+            ((x_cm, np.int32), (y_cm, np.int32), (z_m, np.float32))]
+    for a in (depth_out, var_out):
+        if a is not None and (a.dtype != np.float32 or not a.flags["C_CONTIGUOUS"]):
+            raise TypeError("outputs must be contiguous float32 numpy arrays")
+    x0, y0, cell, nx, ny = (int(v) for v in grid_spec)
+    r = Request()
+    r.x_cm, r.y_cm, r.z_m = (a.ctypes.data for a in arrs)
+    r.n = int(arrs[0].size)
+    r.x0_cm, r.y0_cm, r.cell_cm, r.nx, r.ny = x0, y0, cell, nx, ny
+    r.method, r.k, r.power = int(method), int(k), float(power)
+    r.variogram = vgm if vgm is not None else variogram()
+    r.depth_out = depth_out.ctypes.data
+    r.var_out = var_out.ctypes.data if var_out is not None else None
+    t = ctypes.c_uint64()
+    check(_lib().bg_submit(ctx, ctypes.byref(r), ctypes.byref(t)), "bg_submit")
+    _inflight[(ctx.value, t.value)] = (arrs, depth_out, var_out)
+    return t.value
+
+
+def poll(ctx, ticket: int):
+    """Result of a finished ticket (then released), or None while it runs."""
+    res = Result()
+    st = check(_lib().bg_poll(ctx, ticket, ctypes.byref(res)), "bg_poll")
+    if st == _capi.BG_PENDING:
+        return None
+    _inflight.pop((ctx.value, ticket), None)
+    return res
+
+
+def wait(ctx, ticket: int, timeout_ms: int = -1):
+    """Block until the ticket finishes (BGError with BG_ERR_TIMEOUT on expiry)."""
+    res = Result()
+    check(_lib().bg_wait(ctx, ticket, int(timeout_ms), ctypes.byref(res)), "bg_wait")
+    _inflight.pop((ctx.value, ticket), None)
+    return res
+
+
+def cancel(ctx, ticket: int) -> None:
+    check(_lib().bg_cancel(ctx, ticket), "bg_cancel")
+
+
+def serve_stats(ctx):
+    """(queued, running, reserved device bytes) of the context's serving loop."""
+    q, r, b = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    check(_lib().bg_serve_stats(ctx, ctypes.byref(q), ctypes.byref(r), ctypes.byref(b)),
+          "bg_serve_stats")
+    return q.value, r.value, b.value
+
+
+def serve_shutdown(ctx) -> None:
+    check(_lib().bg_serve_shutdown(ctx), "bg_serve_shutdown")
 
 
 def _check_dtype(t, name):

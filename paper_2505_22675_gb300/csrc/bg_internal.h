@@ -59,12 +59,7 @@ struct OkParams {
 
 // ---------------------------------------------------------------- handles
 
-struct Ctx;
-
-struct DevBuf {
-    void* ptr = nullptr;
-    size_t bytes = 0;
-};
+struct Server;  // serving state of a context (serve.cu)
 
 }  // namespace bg
 
@@ -77,7 +72,7 @@ struct bg_ctx_s {
     std::mutex pin_mu;                 // guards h_pinned
     int32_t* h_pinned = nullptr;       // pinned host scratch for the bbox read-back
     int n_grids = 0, n_soundings = 0;
-    struct Server* server = nullptr;   // serving state (lazily created)
+    bg::Server* server = nullptr;      // serving state (created by the first bg_submit)
 };
 
 struct bg_grid_s {
@@ -102,10 +97,25 @@ namespace bg {
 bg_status dalloc(bg_ctx_s* ctx, void** p, size_t bytes, cudaStream_t st);
 void dfree(bg_ctx_s* ctx, void* p, size_t bytes, cudaStream_t st);
 
+// Bounding box and validity of soundings already scanned on the host.
+struct HostBBox {
+    int32_t x0, y0, x1, y1;   // min / max over valid soundings
+    int64_t n_valid;
+    int32_t out_of_range;     // valid soundings outside (-2^30, 2^30)
+};
+
 // Hash build: validate + pack + bbox, then counting sort and lookup tables.
+// With `known`, the bounding box comes from the caller and the stream is
+// never synchronized.
 bg_status build_soundings(bg_ctx_s* ctx, const int32_t* x, const int32_t* y, const float* z,
                           int64_t n, int on_device, int32_t cell_hint, cudaStream_t st,
-                          bg_soundings_s* s);
+                          bg_soundings_s* s, const HostBBox* known = nullptr);
+
+// Device bytes a hash build over n soundings (n_valid of them valid) may hold.
+size_t soundings_bytes_estimate(int64_t n, int64_t n_valid);
+
+// Free a soundings handle's device memory (stream-ordered on st).
+void free_soundings(bg_soundings_s* s, cudaStream_t st);
 
 // Start half-width (cells) for the k-NN bound search at this k.
 int32_t start_halfwidth(const bg_soundings_s* s, int k);

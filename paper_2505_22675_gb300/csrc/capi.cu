@@ -72,6 +72,23 @@ void dfree(bg_ctx_s* ctx, void* p, size_t bytes, cudaStream_t st) {
     ctx->in_use.fetch_sub((int64_t)bytes);
 }
 
+void free_soundings(bg_soundings_s* s, cudaStream_t st) {
+    bg_ctx_s* ctx = s->ctx;
+    const size_t ncells = (size_t)s->info.ncx * (size_t)s->info.ncy;
+    dfree(ctx, s->d_orig, (size_t)s->info.n_total * 16, st);
+    if (s->d_cell_start) dfree(ctx, s->d_cell_start, (ncells + 1) * 4, st);
+    if (s->d_sat) dfree(ctx, s->d_sat, (size_t)(s->info.ncx + 1) * (s->info.ncy + 1) * 4, st);
+    if (s->d_rec) dfree(ctx, s->d_rec, (size_t)s->info.n_valid * 16, st);
+    s->d_orig = s->d_cell_start = s->d_sat = s->d_rec = nullptr;
+}
+
+size_t soundings_bytes_estimate(int64_t n, int64_t n_valid) {
+    // records (2 x 16 B), cell tables (~2 soundings per cell: cell_start + SAT
+    // + counts), host staging (12 B), small scratch
+    return (size_t)n * 16 + (size_t)n_valid * 16 + (size_t)n * 12 + (size_t)n_valid * 8 +
+           (size_t)(1 << 20);
+}
+
 }  // namespace bg
 
 using namespace bg;
@@ -150,8 +167,6 @@ bg_status bg_ctx_device_bytes(bg_ctx_t ctx, int64_t* out) {
     return BG_OK;
 }
 
-bg_status bg_serve_shutdown(bg_ctx_t ctx);  // serve.cu
-
 bg_status bg_ctx_destroy(bg_ctx_t ctx) {
     BG_REQUIRE(ctx, "ctx is NULL");
     BG_REQUIRE(ctx->n_grids == 0 && ctx->n_soundings == 0,
@@ -212,10 +227,7 @@ bg_status bg_soundings_upload(bg_ctx_t ctx, const int32_t* x_cm, const int32_t* 
     const cudaStream_t st = (cudaStream_t)cuda_stream;
     const bg_status rc = build_soundings(ctx, x_cm, y_cm, z_m, n, on_device, cell_cm_hint, st, s);
     if (rc != BG_OK) {
-        dfree(ctx, s->d_orig, (size_t)n * 16, st);
-        if (s->d_cell_start) dfree(ctx, s->d_cell_start, (size_t)(s->info.ncx * (int64_t)s->info.ncy + 1) * 4, st);
-        if (s->d_sat) dfree(ctx, s->d_sat, (size_t)(s->info.ncx + 1) * (s->info.ncy + 1) * 4, st);
-        if (s->d_rec) dfree(ctx, s->d_rec, (size_t)s->info.n_valid * 16, st);
+        free_soundings(s, st);
         delete s;
         return rc;
     }
@@ -239,11 +251,7 @@ bg_status bg_soundings_destroy(bg_soundings_t s) {
     DeviceGuard dg(ctx->device);
     // stream-ordered frees on the legacy stream: work already queued on other
     // streams that reads this handle must be complete (the caller's contract)
-    const size_t ncells = (size_t)s->info.ncx * (size_t)s->info.ncy;
-    dfree(ctx, s->d_orig, (size_t)s->info.n_total * 16, 0);
-    if (s->d_cell_start) dfree(ctx, s->d_cell_start, (ncells + 1) * 4, 0);
-    if (s->d_sat) dfree(ctx, s->d_sat, (size_t)(s->info.ncx + 1) * (s->info.ncy + 1) * 4, 0);
-    if (s->d_rec) dfree(ctx, s->d_rec, (size_t)s->info.n_valid * 16, 0);
+    free_soundings(s, 0);
     {
         std::lock_guard<std::mutex> lk(ctx->mu);
         ctx->n_soundings--;

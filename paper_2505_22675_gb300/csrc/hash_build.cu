@@ -297,7 +297,7 @@ struct Scratch {
 
 bg_status build_soundings(bg_ctx_s* ctx, const int32_t* x, const int32_t* y, const float* z,
                           int64_t n, int on_device, int32_t cell_hint, cudaStream_t st,
-                          bg_soundings_s* s) {
+                          bg_soundings_s* s, const HostBBox* known) {
     bg_status rc = BG_OK;
     const int32_t *dx = x, *dy = y;
     const float* dz = z;
@@ -338,7 +338,15 @@ bg_status build_soundings(bg_ctx_s* ctx, const int32_t* x, const int32_t* y, con
     }
     BG_CUDA(cudaGetLastError());
     int32_t a[6];
-    {
+    if (known) {
+        // the caller scanned the (host) input already: no device round trip
+        a[0] = known->x0;
+        a[1] = known->y0;
+        a[2] = known->x1;
+        a[3] = known->y1;
+        a[4] = (int32_t)known->n_valid;
+        a[5] = known->out_of_range;
+    } else {
         std::lock_guard<std::mutex> lk(ctx->pin_mu);
         BG_CUDA(cudaMemcpyAsync(ctx->h_pinned, acc, 6 * sizeof(int), cudaMemcpyDeviceToHost, st));
         BG_CUDA(cudaStreamSynchronize(st));
