@@ -205,6 +205,55 @@ bg_status bg_serve_stats(bg_ctx_t ctx, int64_t* queued, int64_t* running, int64_
  * bg_ctx_destroy). */
 bg_status bg_serve_shutdown(bg_ctx_t ctx);
 
+/* ---------------------------------------------------------------- batches */
+
+typedef struct bg_batch_s* bg_batch_t;
+
+/* One tile of a batch: like bg_request, but inputs and outputs are DEVICE
+ * pointers that stay valid (same addresses) for the life of the batch; their
+ * contents may change between runs. */
+typedef struct bg_tile {
+    const int32_t* x_cm;       /* n soundings (device) */
+    const int32_t* y_cm;
+    const float* z_m;          /* NaN = invalid sounding */
+    int64_t n;
+    int32_t x0_cm, y0_cm, cell_cm, nx, ny;   /* output grid, as bg_grid_create */
+    int32_t method;            /* 0 = IDW, 1 = ordinary kriging */
+    int32_t k;                 /* neighbours, [1, 32] */
+    float power;               /* IDW exponent (> 0) */
+    bg_variogram variogram;    /* kriging model */
+    float* depth_out;          /* device, nx*ny */
+    float* var_out;            /* device, nx*ny kriging variance, or NULL */
+} bg_tile;
+
+/* Lay out a batch of tiles of uneven size: one set of device buffers for all
+ * of them (charged to the context's budget), per-tile work descriptors on the
+ * device, and the item lists of the persistent kernels. Results equal the
+ * per-grid calls (bg_soundings_upload + bg_interp_idw / bg_interp_okrige)
+ * bit for bit. The tiles array is copied. */
+bg_status bg_batch_create(bg_ctx_t ctx, const bg_tile* tiles, int n_tiles, bg_batch_t* out);
+
+/* Grid every tile of the batch, ordered after prior work on cuda_stream and
+ * before later work on it. The first run records the launch sequence (hash
+ * build for all tiles, one persistent k-NN/IDW kernel, one persistent solve
+ * kernel per kriging system size) as a CUDA graph; later runs replay it, with
+ * no host synchronization. */
+bg_status bg_batch_run(bg_batch_t b, void* cuda_stream);
+
+/* Hash cell side as a target number of soundings per cell (default 2); the
+ * next run records a new graph. */
+bg_status bg_batch_set_cell_target(bg_batch_t b, float soundings_per_cell);
+
+/* Autotune the cell target: time a few targets on this batch (each run is a
+ * real run, so outputs are written) and keep the fastest; *best_out gets it. */
+bg_status bg_batch_tune(bg_batch_t b, void* cuda_stream, float* best_out);
+
+/* After the last run has finished: bit 0 = a tile had a coordinate outside
+ * (-2^30, 2^30) and yields NaN; bit 1 = some node needed the wide-key pass. */
+bg_status bg_batch_status(bg_batch_t b, int* flags);
+
+bg_status bg_batch_destroy(bg_batch_t b);
+
 /* ------------------------------------------------- allocation-free IDW */
 
 /* IDW gridding that allocates no device memory, for callers that cannot call

@@ -28,7 +28,8 @@ __all__ = [
     "version", "launch_count", "ctx_create", "ctx_destroy", "ctx_device_bytes", "grid_create", "grid_destroy",
     "soundings_upload", "soundings_info", "soundings_destroy", "interp_idw", "interp_okrige",
     "variogram", "interp_idw_noalloc", "submit", "poll", "wait", "cancel", "serve_stats",
-    "serve_shutdown", "Request", "Result",
+    "serve_shutdown", "Request", "Result", "Batch", "batch_create", "batch_run", "batch_tune",
+    "batch_set_cell_target", "batch_status", "batch_destroy",
 ]
 
 
@@ -243,6 +244,71 @@ def serve_stats(ctx):
 
 def serve_shutdown(ctx) -> None:
     check(_lib().bg_serve_shutdown(ctx), "bg_serve_shutdown")
+
+
+class Batch:
+    """Handle of a batch of tiles (bg_batch_t) with references to its tensors."""
+
+    def __init__(self, handle, keep):
+        self.handle = handle
+        self._keep = keep
+
+
+def batch_create(ctx, tiles) -> Batch:
+    """Lay out a batch. tiles: sequence of dicts with device tensors x_cm, y_cm
+    (int32), z_m (float32), grid_spec (x0, y0, cell, nx, ny), method, k, and
+    outputs depth_out (float32, nx*ny), var_out (kriging, or None); plus power
+    (IDW) or vgm (kriging)."""
+    arr = (_capi.Tile * max(1, len(tiles)))()
+    keep = []
+    for i, t in enumerate(tiles):
+        for name, dt in (("x_cm", "int32"), ("y_cm", "int32"), ("z_m", "float32"),
+                         ("depth_out", "float32")):
+            _check_dtype(t[name], dt)
+            if not _is_cuda(t[name]):
+                raise ValueError(f"tile {i}: {name} must be a device tensor")
+        r = arr[i]
+        r.x_cm, r.y_cm, r.z_m = (t[n].data_ptr() for n in ("x_cm", "y_cm", "z_m"))
+        r.n = int(t["x_cm"].shape[0])
+        r.x0_cm, r.y0_cm, r.cell_cm, r.nx, r.ny = (int(v) for v in t["grid_spec"])
+        r.method, r.k = int(t["method"]), int(t["k"])
+        r.power = float(t.get("power", 2.0))
+        r.variogram = t.get("vgm") or variogram()
+        r.depth_out = t["depth_out"].data_ptr()
+        vo = t.get("var_out")
+        r.var_out = vo.data_ptr() if vo is not None else None
+        keep.append(t)
+    out = ctypes.c_void_p()
+    check(_lib().bg_batch_create(ctx, arr, len(tiles), ctypes.byref(out)), "bg_batch_create")
+    return Batch(out, keep)
+
+
+def batch_run(b: Batch, stream=None) -> None:
+    check(_lib().bg_batch_run(b.handle, _stream(stream, *(t["depth_out"] for t in b._keep[:1]))),
+          "bg_batch_run")
+
+
+def batch_set_cell_target(b: Batch, soundings_per_cell: float) -> None:
+    check(_lib().bg_batch_set_cell_target(b.handle, float(soundings_per_cell)),
+          "bg_batch_set_cell_target")
+
+
+def batch_tune(b: Batch, stream=None) -> float:
+    best = ctypes.c_float()
+    check(_lib().bg_batch_tune(b.handle, _stream(stream, *(t["depth_out"] for t in b._keep[:1])),
+                               ctypes.byref(best)), "bg_batch_tune")
+    return best.value
+
+
+def batch_status(b: Batch) -> int:
+    f = ctypes.c_int()
+    check(_lib().bg_batch_status(b.handle, ctypes.byref(f)), "bg_batch_status")
+    return f.value
+
+
+def batch_destroy(b: Batch) -> None:
+    check(_lib().bg_batch_destroy(b.handle), "bg_batch_destroy")
+    b._keep = []
 
 
 def _check_dtype(t, name):

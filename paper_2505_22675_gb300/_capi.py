@@ -51,6 +51,10 @@ class Request(ctypes.Structure):
                 ("depth_out", ctypes.c_void_p), ("var_out", ctypes.c_void_p)]
 
 
+# bg_tile has bg_request's layout; its pointers are device addresses
+Tile = Request
+
+
 class Result(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("nodes", ctypes.c_int64),
                 ("t_submit_us", ctypes.c_double), ("t_start_us", ctypes.c_double),
@@ -87,6 +91,12 @@ _SIGNATURES = {
     "bg_serve_stats": ([P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                         ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
     "bg_serve_shutdown": ([P], ctypes.c_int),
+    "bg_batch_create": ([P, ctypes.POINTER(Request), ctypes.c_int, PP], ctypes.c_int),
+    "bg_batch_run": ([P, P], ctypes.c_int),
+    "bg_batch_set_cell_target": ([P, ctypes.c_float], ctypes.c_int),
+    "bg_batch_tune": ([P, P, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
+    "bg_batch_status": ([P, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "bg_batch_destroy": ([P], ctypes.c_int),
     "bg_interp_idw_noalloc": ([P, P, P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int,
                                ctypes.c_float, P, P, P], ctypes.c_int),

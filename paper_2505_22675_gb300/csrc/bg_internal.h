@@ -138,6 +138,11 @@ struct HashArena {
 bg_status build_hash_in_arena(const int32_t* x, const int32_t* y, const float* z, int64_t n,
                               const HashArena& ar, cudaStream_t st, bg_soundings_s* s);
 
+// Exclusive scan of n ints into out[0..n] (out[n] = total); out2 (may alias
+// in) gets a copy of out[0..n). bsum: scan_blocks(n) + 1 ints of scratch.
+int scan_blocks(int64_t n);
+void launch_excl_scan(const int* in, int64_t n, int* out, int* out2, int* bsum, cudaStream_t st);
+
 // IDW launch with a caller-provided device flag (one int) instead of an allocated one.
 bg_status launch_idw_with_flag(const bg_soundings_s* s, const GridView& g, int k, float power,
                                float* depth, int32_t* nbr, int* d_flag, cudaStream_t st);

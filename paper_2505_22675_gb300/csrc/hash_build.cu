@@ -539,4 +539,14 @@ bg_status build_hash_in_arena(const int32_t* x, const int32_t* y, const float* z
     return BG_OK;
 }
 
+int scan_blocks(int64_t n) { return (int)((n + kScanTile - 1) / kScanTile); }
+
+void launch_excl_scan(const int* in, int64_t n, int* out, int* out2, int* bsum, cudaStream_t st) {
+    const int nb = scan_blocks(n);
+    k_scan_reduce<<<nb, kThreads, 0, st>>>(in, n, bsum);
+    k_scan_blocksums<<<1, kThreads, 0, st>>>(bsum, nb, out + n);
+    k_scan_apply<<<nb, kThreads, 0, st>>>(in, n, bsum, out, out2);
+    note_launches(3);
+}
+
 }  // namespace bg

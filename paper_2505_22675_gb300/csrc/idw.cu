@@ -1,96 +1,11 @@
-// Fused exact k-NN + inverse-distance weighting, one thread per grid node.
-//
-// zhat = sum w_i z_i / sum w_i with w_i = d_i^-p over the k nearest valid
-// soundings. It is evaluated as z_1 + sum w_i (z_i - z_1) / sum w_i with
-// z_1 the nearest sounding's depth and w_i = (d_1^2 / d_i^2)^(p/2): the same
-// quantity, but every term is an anomaly of a few metres (so only the final
-// add rounds at ~3500 m) and every weight is in (0, 1]. Accumulation follows
-// the ascending (d2, index) order, so a node's result does not depend on the
-// cell size, the launch shape or what else runs.
+// Fused exact k-NN + inverse-distance weighting: per-grid kernels and launchers.
+// The device code is in idw_dev.cuh.
 #include <algorithm>
-#include <cmath>
 
-#include "bg_internal.h"
-#include "knn.cuh"
+#include "idw_dev.cuh"
 
 namespace bg {
 namespace {
-
-// IDW from the neighbours in ascending (d2, index) order; get(i) returns
-// (d2, upload index) of the i-th.
-template <class Get>
-__device__ __forceinline__ float idw_from(const HashView& h, int keff, float power, Get get) {
-    if (keff == 0) return __int_as_float(0x7fc00000);  // NaN: no valid sounding
-    const int* zb = reinterpret_cast<const int*>(h.orig) + 2;  // z bits of record i at zb[4*i]
-    uint64_t d0;
-    int i0;
-    get(0, d0, i0);
-    const float z1 = __int_as_float(__ldg(zb + 4 * (int64_t)i0));
-    if (d0 == 0) return z1;  // node on top of a sounding
-    const float d1 = (float)d0;
-    const float l1 = log2f(d1);
-    const float hp = 0.5f * power;
-    float num = 0.0f, den = 1.0f;  // i = 0 contributes w = 1, anomaly 0
-    for (int i = 1; i < keff; ++i) {
-        uint64_t di2;
-        int ii;
-        get(i, di2, ii);
-        const float zi = __int_as_float(__ldg(zb + 4 * (int64_t)ii));
-        const float di = (float)di2;
-        const float w = (power == 2.0f) ? d1 / di : exp2f(hp * (l1 - log2f(di)));
-        num = fmaf(w, zi - z1, num);
-        den += w;
-    }
-    return z1 + num / den;
-}
-
-template <int K, bool kWide>
-__device__ __forceinline__ void idw_node(const HashView& h, const GridView& g, int k, float power,
-                                         float* __restrict__ depth, int32_t* __restrict__ nbr,
-                                         int* __restrict__ flag, NodeIdx nd, uint64_t* hp) {
-    if (nd.i >= g.nx || nd.j >= g.ny) return;
-    const int64_t node = (int64_t)nd.j * g.nx + nd.i;
-    const int qx = g.x0 + nd.i * g.cell + g.cell / 2;
-    const int qy = g.y0 + nd.j * g.cell + g.cell / 2;
-    int32_t* o = nbr ? nbr + node * k : nullptr;
-    if (h.n_valid == 0) {
-        if (kWide) return;
-        depth[node] = __int_as_float(0x7fc00000);
-        if (o)
-            for (int i = 0; i < k; ++i) o[i] = -1;
-        return;
-    }
-    const Bound b = knn_bound<K>(h, qx, qy);
-    const bool fits = packed_fits(h, b.tau0);
-    if constexpr (kWide) {
-        if (fits) return;  // done by the packed pass
-        uint64_t d2[K];
-        int id[K];
-        const int keff = min(knn_scan<K, true>(h, qx, qy, b, d2, id), k);
-        depth[node] = idw_from(h, keff, power, [&](int i, uint64_t& dd, int& ii) {
-            // the register arrays are read with a runtime index only here, in the rare wide pass
-            dd = d2[i];
-            ii = id[i];
-        });
-        if (o)
-            for (int i = 0; i < k; ++i) o[i] = i < keff ? id[i] : -1;
-    } else {
-        if (!fits) {
-            *flag = 1;  // the wide pass picks this node up
-            return;
-        }
-        const int keff = min(knn_scan_heap<K, 128>(h, qx, qy, b, hp), k);
-        const int bits = h.idx_bits;
-        const uint64_t mask = (1ull << bits) - 1;
-        depth[node] = idw_from(h, keff, power, [&](int i, uint64_t& dd, int& ii) {
-            const uint64_t key = hp[i * 128];
-            dd = key >> bits;
-            ii = (int)(key & mask);
-        });
-        if (o)
-            for (int i = 0; i < k; ++i) o[i] = i < keff ? (int)(hp[i * 128] & mask) : -1;
-    }
-}
 
 // Packed pass: one 16 x 8 node patch per block.
 template <int K>

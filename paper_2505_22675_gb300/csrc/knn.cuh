@@ -62,9 +62,8 @@ struct Bound {
     int cy;         // the node's (clamped) cell row
 };
 
-// Phase 1: the smallest square around the node's cell holding >= K soundings.
-template <int K>
-__device__ __forceinline__ Bound knn_bound(const HashView& h, int qx, int qy) {
+// Phase 1: the smallest square around the node's cell holding >= kc soundings.
+__device__ __forceinline__ Bound knn_bound_rt(const HashView& h, int qx, int qy, int kc) {
     const int cx = clamp_cell(h, (int64_t)qx - h.hx0, h.ncx);
     const int cy = clamp_cell(h, (int64_t)qy - h.hy0, h.ncy);
     const int rmax = max(max(cx, h.ncx - 1 - cx), max(cy, h.ncy - 1 - cy));
@@ -74,7 +73,7 @@ __device__ __forceinline__ Bound knn_bound(const HashView& h, int qx, int qy) {
     };
     int r = min(h.r0, rmax);
     int lo, hi;
-    if (cnt(r) >= K) {
+    if (cnt(r) >= kc) {
         lo = -1;
         hi = r;
     } else {
@@ -82,13 +81,13 @@ __device__ __forceinline__ Bound knn_bound(const HashView& h, int qx, int qy) {
         hi = r;
         while (hi < rmax) {
             hi = min(2 * hi + 1, rmax);
-            if (cnt(hi) >= K) break;
+            if (cnt(hi) >= kc) break;
             lo = hi;
         }
     }
-    while (hi - lo > 1) {  // invariant: cnt(lo) < K (or lo = -1), cnt(hi) >= K
+    while (hi - lo > 1) {  // invariant: cnt(lo) < kc (or lo = -1), cnt(hi) >= kc
         const int mid = (lo + hi) >> 1;
-        if (cnt(mid) >= K)
+        if (cnt(mid) >= kc)
             hi = mid;
         else
             lo = mid;
@@ -102,6 +101,11 @@ __device__ __forceinline__ Bound knn_bound(const HashView& h, int qx, int qy) {
     const int64_t mdx = max((int64_t)qx - xlo, xhi - (int64_t)qx);
     const int64_t mdy = max((int64_t)qy - ylo, yhi - (int64_t)qy);
     return Bound{mdx * mdx + mdy * mdy, cy};
+}
+
+template <int K>
+__device__ __forceinline__ Bound knn_bound(const HashView& h, int qx, int qy) {
+    return knn_bound_rt(h, qx, qy, K);
 }
 
 // Does (tau0 + 1) << idx_bits fit in 64 bits?
@@ -250,10 +254,10 @@ __device__ __forceinline__ void heap_build(uint64_t* hp, int n) {
 }
 
 // Phase 2 with the heap. On return hp[0 .. keff) holds the neighbours' packed
-// keys in ascending order; returns keff (<= K). Requires packed_fits(tau0).
-template <int K, int S>
-__device__ __forceinline__ int knn_scan_heap(const HashView& h, int qx, int qy, const Bound& b,
-                                             uint64_t* hp) {
+// keys in ascending order; returns keff (<= kc). Requires packed_fits(tau0).
+template <int S>
+__device__ __forceinline__ int knn_scan_heap_rt(const HashView& h, int qx, int qy, const Bound& b,
+                                                uint64_t* hp, int kc) {
     const int bits = h.idx_bits;
     const int64_t tau0 = b.tau0;
     const uint64_t sentinel = (uint64_t)(tau0 + 1) << bits;
@@ -292,14 +296,14 @@ __device__ __forceinline__ int knn_scan_heap(const HashView& h, int qx, int qy, 
             if (d2 > utau) continue;
             const uint64_t c = (d2 << bits) | (uint32_t)v.w;
             if (c < root) {
-                if (cnt < K) {
+                if (cnt < kc) {
                     hp[cnt * S] = c;
-                    if (++cnt == K) {
-                        heap_build<S>(hp, K);
+                    if (++cnt == kc) {
+                        heap_build<S>(hp, kc);
                         root = hp[0];
                     }
                 } else {
-                    heap_sift_down<S>(hp, 0, K, c);
+                    heap_sift_down<S>(hp, 0, kc, c);
                     root = hp[0];
                 }
             }
@@ -307,13 +311,19 @@ __device__ __forceinline__ int knn_scan_heap(const HashView& h, int qx, int qy, 
         tau = min(tau, (int64_t)(root >> bits));
     }
     // heapsort into ascending order
-    if (cnt < K) heap_build<S>(hp, cnt);
+    if (cnt < kc) heap_build<S>(hp, cnt);
     for (int e = cnt - 1; e > 0; --e) {
         const uint64_t v = hp[e * S];
         hp[e * S] = hp[0];
         heap_sift_down<S>(hp, 0, e, v);
     }
     return cnt;
+}
+
+template <int K, int S>
+__device__ __forceinline__ int knn_scan_heap(const HashView& h, int qx, int qy, const Bound& b,
+                                             uint64_t* hp) {
+    return knn_scan_heap_rt<S>(h, qx, qy, b, hp, K);
 }
 
 // Grid node (i, j) owned by this thread inside the 16 x 8 node patch (px, py).

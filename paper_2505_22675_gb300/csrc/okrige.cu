@@ -1,128 +1,12 @@
-// Local ordinary kriging (Sec. III-C) over the exact k nearest soundings.
-//
-// Two kernels per chunk of grid rows:
-//   k_knn_ids<K>      one thread per node: exact k-NN (knn.cuh), writes the
-//                     neighbours' upload indices (ascending) to an id buffer;
-//   k_okrige_solve<K> G = K/4 threads per kriging system, 32/G systems per
-//                     warp: each thread owns R = 4 rows of its system.
-//
-// The bordered variogram system [Gamma 1; 1^T 0][lambda; mu] = [gamma_0; 1]
-// is reduced with sum(lambda) = 1 by eliminating lambda_0 (the nearest
-// neighbour) and mu. For reduced rows r, c (neighbours r+1, c+1):
-//     A[r][c] = Gamma_r0 + Gamma_c0 - Gamma_rc,   b_r = Gamma_r0 + gamma_00 - gamma_r0,
-//     A lambda' = b,  lambda_0 = 1 - sum(lambda'),  mu = gamma_00 - sum_a Gamma_0a lambda_a.
-// A is symmetric positive definite for a conditionally negative definite
-// variogram (spherical and exponential are, in 2-D). It is factored by
-// Cholesky in FP32 with the lower triangle in registers (thread t, slot s
-// holds row G*s + t, columns 0 .. G*(s+1)-1); pivots and column entries move
-// between the G threads of a system by warp shuffles. One refinement step
-// follows: the residual b - A lambda' is accumulated from exact products
-// (FMA error terms) and error-free sums as an FP32 double-word (about 48
-// significant bits) against the original A kept in shared memory, and the
-// correction reuses the factor. The weight sum closes in FP64:
-// lambda_0 = 1 - sum(lambda'). Outputs:
-//     zhat    = z_0 + sum_a lambda_a (z_a - z_0)          (= sum lambda_i z_i)
-//     sigma^2 = lambda_0 gamma_00 + sum_a lambda_a gamma_a0 + mu.
-// Rows beyond k_eff - 1 are identity rows with zero right-hand side, so every
-// system has the fixed size K and all loops over rows and columns unroll.
+// Local ordinary kriging (Sec. III-C): the per-grid kernels and their launcher.
+// The device code (k-NN to ids, reduced-system assembly, Cholesky, refinement)
+// is in okrige_dev.cuh; see there for the formulation.
 #include <algorithm>
-#include <cmath>
-#include <utility>
 
-#include "bg_internal.h"
-#include "knn.cuh"
+#include "okrige_dev.cuh"
 
 namespace bg {
 namespace {
-
-constexpr int kR = 4;            // rows per thread
-constexpr int kSolveWarps = 2;   // warps per solve block
-constexpr int kRounds = 8;       // system batches per warp
-
-template <int K>
-struct Geo {
-    static constexpr int G = K / kR;                      // threads per system
-    static constexpr int SYS = 32 / G;                    // systems per warp
-    static constexpr int LEN = G * kR * (kR + 1) / 2;     // register floats of L
-    static constexpr int ROW = K + 1;                     // smem row stride (bank = row + col)
-    static constexpr int TAB = K + 1;                     // neighbour table length
-    // per system: one K x (K+1) matrix (lower = fixed-point A, upper = factor
-    // transposed) and three neighbour tables; the stride is = G (mod 32) so
-    // that the G-thread groups of a warp cover all 32 banks
-    static constexpr int RAW = K * ROW + 3 * TAB;
-    static constexpr int SYS_FLOATS = RAW + ((G - RAW % 32) + 32) % 32;
-    static constexpr int WARP_FLOATS = SYS * SYS_FLOATS;
-    static __host__ __device__ constexpr int off(int s) { return G * s * (s + 1) / 2; }
-};
-
-__device__ __forceinline__ float variogram(const OkParams& p, float h_m) {
-    if (p.model == BG_VARIOGRAM_SPHERICAL) {
-        const float t = h_m * p.inv_a;
-        if (t >= 1.0f) return p.sill;
-        return fmaf(p.c * t, fmaf(-0.5f * t, t, 1.5f), p.c0);
-    }
-    return fmaf(p.c, 1.0f - __expf(-h_m * p.inv_a), p.c0);
-}
-
-// gamma from a separation in cm; zero separation gives `at_zero`
-__device__ __forceinline__ float gamma_cm(const OkParams& p, int dx, int dy, float at_zero) {
-    if ((dx | dy) == 0) return at_zero;
-    const float fx = (float)dx, fy = (float)dy;
-    const float d2 = fmaf(fx, fx, fy * fy);
-    return variogram(p, d2 * rsqrtf(d2) * 0.01f);
-}
-
-// gamma between two distinct soundings from float offsets in cm (exact
-// integers below 2^24); zero separation gives the nugget c0 (the h -> 0+
-// limit) without a branch: t = min(h/a, 1) makes the spherical model's
-// polynomial equal the sill beyond the range
-__device__ __forceinline__ float gamma_pair_f(const OkParams& p, float dx, float dy) {
-    const float d2 = fmaf(dx, dx, dy * dy);
-    const float h_cm = d2 * rsqrtf(d2 + 1e-30f);
-    if (p.model == BG_VARIOGRAM_SPHERICAL) {
-        const float t = fminf(h_cm * p.inv_a * 0.01f, 1.0f);
-        return fmaf(p.c * t, fmaf(-0.5f * t, t, 1.5f), p.c0);
-    }
-    return fmaf(p.c, 1.0f - __expf(-h_cm * p.inv_a * 0.01f), p.c0);
-}
-
-// ------------------------------------------------------------ k-NN -> ids
-
-template <int K, bool kWide>
-__device__ __forceinline__ void knn_ids_node(const HashView& h, const GridView& g, int k,
-                                             int64_t node0, int32_t* __restrict__ ids,
-                                             int* __restrict__ flag, NodeIdx nd, int j1,
-                                             uint64_t* hp) {
-    if (nd.i >= g.nx || nd.j >= j1) return;
-    const int64_t node = (int64_t)nd.j * g.nx + nd.i;
-    const int qx = g.x0 + nd.i * g.cell + g.cell / 2;
-    const int qy = g.y0 + nd.j * g.cell + g.cell / 2;
-    int32_t* o = ids + (node - node0) * k;
-    if (h.n_valid == 0) {
-        if (!kWide)
-            for (int i = 0; i < k; ++i) o[i] = -1;
-        return;
-    }
-    const Bound b = knn_bound<K>(h, qx, qy);
-    const bool fits = packed_fits(h, b.tau0);
-    if constexpr (kWide) {
-        if (fits) return;
-        uint64_t d2[K];
-        int id[K];
-        const int keff = knn_scan<K, true>(h, qx, qy, b, d2, id);
-#pragma unroll
-        for (int i = 0; i < K; ++i)
-            if (i < k) o[i] = i < keff ? id[i] : -1;
-    } else {
-        if (!fits) {
-            *flag = 1;
-            return;
-        }
-        const int keff = knn_scan_heap<K, 128>(h, qx, qy, b, hp);
-        const uint64_t mask = (1ull << h.idx_bits) - 1;
-        for (int i = 0; i < k; ++i) o[i] = i < keff ? (int)(hp[i * 128] & mask) : -1;
-    }
-}
 
 // grid rows [j0, j1); j0 is a multiple of 8
 template <int K>
@@ -150,288 +34,12 @@ __global__ void __launch_bounds__(128) k_knn_ids_wide(HashView h, GridView g, in
                               nullptr);
 }
 
-// ---------------------------------------------------------------- solve
-
-__host__ __device__ constexpr int tri(int r) { return r * (r + 1) / 2; }
-
-// Cholesky column j of the register-held lower triangle: scale by the pivot,
-// then update the trailing rows with column j broadcast within the group.
-// Expanded over j with an integer_sequence so every register index is a
-// compile-time constant (a nested #pragma unroll over the whole triangle is
-// beyond the unroller and would leave L in local memory).
-template <int K, int J>
-__device__ __forceinline__ void chol_column(float (&L)[Geo<K>::LEN], float (&dinv)[kR], int t,
-                                            int gbase) {
-    using Gm = Geo<K>;
-    constexpr int G = Gm::G;
-    constexpr int SJ = J / G;
-    const float d = __shfl_sync(kFull, L[Gm::off(SJ) + J], gbase + J % G);
-    const float inv = rsqrtf(d);
-#pragma unroll
-    for (int s = 0; s < kR; ++s) {
-        if (G * (s + 1) - 1 >= J) {
-            const int r = G * s + t;
-            if (r > J) L[Gm::off(s) + J] *= inv;
-            if (r == J) {
-                L[Gm::off(s) + J] = d * inv;
-                dinv[s] = inv;
-            }
-        }
-    }
-#pragma unroll
-    for (int c = J + 1; c < K; ++c) {
-        const float lcj = __shfl_sync(kFull, L[Gm::off(c / G) + J], gbase + c % G);
-#pragma unroll
-        for (int s = 0; s < kR; ++s)
-            if (G * (s + 1) - 1 >= c) L[Gm::off(s) + c] = fmaf(-L[Gm::off(s) + J], lcj, L[Gm::off(s) + c]);
-    }
-}
-
-template <int K, int... J>
-__device__ __forceinline__ void chol_factor(float (&L)[Geo<K>::LEN], float (&dinv)[kR], int t,
-                                            int gbase, std::integer_sequence<int, J...>) {
-    (chol_column<K, J>(L, dinv, t, gbase), ...);
-}
-
-// forward sweep step j of L y = v (L rows in registers)
-template <int K, int J>
-__device__ __forceinline__ void fwd_step(const float (&L)[Geo<K>::LEN], const float (&dinv)[kR],
-                                         float (&v)[kR], int t, int gbase) {
-    using Gm = Geo<K>;
-    constexpr int G = Gm::G;
-    constexpr int SJ = J / G;
-    if (t == J % G) v[SJ] *= dinv[SJ];
-    const float yj = __shfl_sync(kFull, v[SJ], gbase + J % G);
-#pragma unroll
-    for (int s = 0; s < kR; ++s)
-        if (G * (s + 1) - 1 > J && G * s + t > J) v[s] = fmaf(-L[Gm::off(s) + J], yj, v[s]);
-}
-
-// transposed sweep for column j = K-1-I of L^T x = y: the owner of row j
-// finishes x_j and broadcasts it; rows r < j subtract L[j][r] x_j, read from
-// the transposed copy of the factor at (r, j) in shared memory
-template <int K, int I>
-__device__ __forceinline__ void bwd_step(const float* Lt, const float (&dinv)[kR], float (&v)[kR],
-                                         int t, int gbase) {
-    using Gm = Geo<K>;
-    constexpr int G = Gm::G;
-    constexpr int J = K - 1 - I;
-    constexpr int SJ = J / G;
-    if (t == J % G) v[SJ] *= dinv[SJ];
-    const float xj = __shfl_sync(kFull, v[SJ], gbase + J % G);
-#pragma unroll
-    for (int s = 0; s < kR; ++s)
-        if (G * s < J && G * s + t < J) v[s] = fmaf(-Lt[(G * s + t) * Gm::ROW + J], xj, v[s]);
-}
-
-template <int K, int... J>
-__device__ __forceinline__ void chol_solve_seq(const float (&L)[Geo<K>::LEN], const float* Lt,
-                                               const float (&dinv)[kR], float (&v)[kR], int t,
-                                               int gbase, std::integer_sequence<int, J...>) {
-    (fwd_step<K, J>(L, dinv, v, t, gbase), ...);
-    (bwd_step<K, J>(Lt, dinv, v, t, gbase), ...);
-}
-
-// 2^e as a float (|e| <= 126)
-__device__ __forceinline__ float pow2f(int e) { return __int_as_float((127 + e) << 23); }
-
-// exponent e with 2^(e-1) <= v < 2^e for finite v > 0
-__device__ __forceinline__ int exp_above(float v) { return ((__float_as_int(v) >> 23) & 0xff) - 126; }
-
 template <int K>
 __global__ void __launch_bounds__(kSolveWarps * 32) k_okrige_solve(
     HashView h, GridView g, int k, OkParams p, int64_t node0, int64_t nodes,
     const int32_t* __restrict__ ids, float* __restrict__ depth, float* __restrict__ var) {
-    using Gm = Geo<K>;
-    constexpr int G = Gm::G;
-    constexpr int ROW = Gm::ROW;
-    __shared__ float smem[kSolveWarps * Gm::WARP_FLOATS];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int grp = lane / G, t = lane % G, gbase = grp * G;
-    float* sysmem = smem + warp * Gm::WARP_FLOATS + grp * Gm::SYS_FLOATS;
-    int* Aq = reinterpret_cast<int*>(sysmem);      // lower triangle: fixed-point A
-    float* Lt = sysmem;                             // strict upper triangle: L transposed
-    float* fx = sysmem + K * ROW;                   // x of neighbour n minus x of neighbour 0 (cm)
-    float* fy = fx + Gm::TAB;                       // y likewise
-    float* tg = fy + Gm::TAB;                       // Gamma(neighbour of row r, neighbour 0)
-    const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << gbase);
-
-    for (int round = 0; round < kRounds; ++round) {
-        const int64_t sys = ((int64_t)blockIdx.x * kSolveWarps + warp) * (Gm::SYS * kRounds) +
-                            (int64_t)round * Gm::SYS + grp;
-        const bool live = sys < nodes;  // uniform within a group
-        const int64_t node = node0 + (live ? sys : 0);
-        const int32_t* my = ids + (live ? sys : 0) * k;
-
-        // neighbour ids of my rows (reduced row r <-> neighbour r + 1) and k_eff;
-        // ids are -1 exactly past k_eff
-        int nid[kR];
-        unsigned cnt = 0;
-#pragma unroll
-        for (int s = 0; s < kR; ++s) {
-            const int n = 1 + G * s + t;
-            nid[s] = (live && n < k) ? __ldg(my + n) : -1;
-            cnt += __popc(__ballot_sync(kFull, nid[s] >= 0) & gmask);
-        }
-        const int id0 = live ? __ldg(my) : -1;
-        const int ke = (id0 >= 0) ? 1 + (int)cnt : 0;  // 0: no output (no data, or past the end)
-        const int qx = g.x0 + (int)(node % g.nx) * g.cell + g.cell / 2;
-        const int qy = g.y0 + (int)(node / g.nx) * g.cell + g.cell / 2;
-
-        // gather the neighbours' records; offsets from neighbour 0 as exact floats
-        int4 r0 = make_int4(0, 0, 0, 0);
-        if (id0 >= 0) r0 = __ldg(h.orig + id0);
-        const float z0 = __int_as_float(r0.z);
-        const float g00 = gamma_cm(p, r0.x - qx, r0.y - qy, 0.0f);
-        float zr[kR], gr0[kR], g0r[kR];  // depth; Gamma(row's neighbour, nbr 0); gamma(node, row's nbr)
-        float gmax = 0.0f;
-#pragma unroll
-        for (int s = 0; s < kR; ++s) {
-            int4 rr = make_int4(0, 0, 0, 0);
-            const bool real = nid[s] >= 0;
-            if (real) rr = __ldg(h.orig + nid[s]);
-            const int r = G * s + t;
-            const float ox = (float)(rr.x - r0.x), oy = (float)(rr.y - r0.y);
-            fx[r + 1] = ox;
-            fy[r + 1] = oy;
-            zr[s] = __int_as_float(rr.z);
-            gr0[s] = real ? gamma_pair_f(p, ox, oy) : 0.0f;
-            g0r[s] = real ? gamma_cm(p, rr.x - qx, rr.y - qy, 0.0f) : 0.0f;
-            tg[r] = gr0[s];
-            gmax = fmaxf(gmax, gr0[s]);
-        }
-#pragma unroll
-        for (int o = 1; o < G; o <<= 1) gmax = fmaxf(gmax, __shfl_xor_sync(kFull, gmax, o));
-        // A is SPD, so |A[r][c]| <= its largest diagonal entry max(1, 2 max Gamma_r0);
-        // fixed point with 30 bits below that bound
-        const int ea = 30 - exp_above(fmaxf(1.0f, 2.0f * gmax));
-        const float sa = pow2f(ea), isa = pow2f(-ea);
-        __syncwarp();
-
-        // assemble the lower triangle once per entry (the group's threads take
-        // the columns c = t, t + G, ... of each row), straight into fixed point
-        for (int r = 0; r < K; ++r) {
-            const bool row = r + 1 < ke;
-            const float xr = fx[r + 1], yr = fy[r + 1], grr = tg[r];
-            for (int c = t; c <= r; c += G) {
-                float v;
-                if (c == r)
-                    v = row ? 2.0f * grr : 1.0f;
-                else
-                    v = (row && c + 1 < ke)
-                            ? (grr + tg[c]) - gamma_pair_f(p, xr - fx[c + 1], yr - fy[c + 1])
-                            : 0.0f;
-                Aq[r * ROW + c] = __float2int_rn(v * sa);
-            }
-        }
-        __syncwarp();
-
-        // my rows into registers (zero above the diagonal)
-        float L[Gm::LEN];
-        float b[kR];
-#pragma unroll
-        for (int s = 0; s < kR; ++s) {
-            const int r = G * s + t;
-            b[s] = (r + 1 < ke) ? (gr0[s] + g00) - g0r[s] : 0.0f;
-#pragma unroll
-            for (int c = 0; c < G * (s + 1); ++c) {
-                const int q = Aq[c <= r ? r * ROW + c : 0];
-                L[Gm::off(s) + c] = c <= r ? (float)q * isa : 0.0f;
-            }
-        }
-
-        // factor in registers; L transposed into the upper triangle for the
-        // back sweeps (row r, column c < r goes to (c, r))
-        float dinv[kR];
-#pragma unroll
-        for (int s = 0; s < kR; ++s) dinv[s] = 1.0f;
-        chol_factor<K>(L, dinv, t, gbase, std::make_integer_sequence<int, K>{});
-#pragma unroll
-        for (int s = 0; s < kR; ++s) {
-            const int r = G * s + t;
-#pragma unroll
-            for (int c = 0; c < G * (s + 1); ++c)
-                if (c < r) Lt[c * ROW + r] = L[Gm::off(s) + c];
-        }
-        __syncwarp();
-
-        // solve, one refinement step, solve again. The residual b - A' x' is
-        // exact: x' is x rounded to 24-bit fixed point (representable in FP32),
-        // A' the 30-bit copy, and the sum of the 2^54-bounded products is
-        // accumulated in 64-bit integers without rounding.
-        float v[kR], x[kR];
-#pragma unroll
-        for (int s = 0; s < kR; ++s) v[s] = b[s];
-#pragma unroll 1
-        for (int pass = 0; pass < 2; ++pass) {
-            chol_solve_seq<K>(L, Lt, dinv, v, t, gbase, std::make_integer_sequence<int, K>{});
-            if (pass == 1) {
-#pragma unroll
-                for (int s = 0; s < kR; ++s) x[s] += v[s];
-                break;
-            }
-            float xmax = 0.0f;
-#pragma unroll
-            for (int s = 0; s < kR; ++s) xmax = fmaxf(xmax, fabsf(v[s]));
-#pragma unroll
-            for (int o = 1; o < G; o <<= 1) xmax = fmaxf(xmax, __shfl_xor_sync(kFull, xmax, o));
-            const int ex = xmax > 0.0f ? 24 - exp_above(xmax) : 0;
-            const float sx = pow2f(ex), isx = pow2f(-ex);
-            int xq[kR];
-            long long acc[kR];
-#pragma unroll
-            for (int s = 0; s < kR; ++s) {
-                xq[s] = __float2int_rn(v[s] * sx);
-                x[s] = (float)xq[s] * isx;
-                acc[s] = __float2ll_rn((b[s] * sa) * sx);
-            }
-#pragma unroll
-            for (int sc = 0; sc < kR; ++sc) {
-#pragma unroll 4
-                for (int tc = 0; tc < G; ++tc) {
-                    const int c = G * sc + tc;
-                    const int xc = __shfl_sync(kFull, xq[sc], gbase + tc);
-#pragma unroll
-                    for (int s = 0; s < kR; ++s) {
-                        const int r = G * s + t;
-                        const int a = Aq[max(r, c) * ROW + min(r, c)];
-                        acc[s] -= (long long)a * (long long)xc;
-                    }
-                }
-            }
-#pragma unroll
-            for (int s = 0; s < kR; ++s) v[s] = ((float)acc[s] * isa) * isx;
-        }
-
-        // weights and outputs; the weight sum closes in FP64
-        float ps = 0.0f, pz = 0.0f, pv = 0.0f;
-#pragma unroll
-        for (int s = 0; s < kR; ++s) {
-            const bool row = G * s + t + 1 < ke;
-            const float lam = row ? x[s] : 0.0f;
-            ps += lam;
-            pz = fmaf(lam, zr[s] - z0, pz);
-            pv = fmaf(lam, g0r[s] - gr0[s], pv);
-        }
-        double wsum = (double)ps;
-#pragma unroll
-        for (int o = 1; o < G; o <<= 1) {
-            wsum += __shfl_xor_sync(kFull, wsum, o);
-            pz += __shfl_xor_sync(kFull, pz, o);
-            pv += __shfl_xor_sync(kFull, pv, o);
-        }
-        const float lam0 = (float)(1.0 - wsum);
-        if (live && t == 0) {
-            if (ke == 0) {
-                depth[node] = __int_as_float(0x7fc00000);  // no valid sounding
-                if (var) var[node] = __int_as_float(0x7fc00000);
-            } else {
-                depth[node] = z0 + pz;
-                if (var) var[node] = fmaf(lam0, g00, g00 + pv);
-            }
-        }
-        __syncwarp();
-    }
+    __shared__ float smem[kSolveWarps * Geo<K>::WARP_FLOATS];
+    okrige_solve_block<K>(h, g, k, p, node0, nodes, ids, depth, var, blockIdx.x, smem);
 }
 
 template <int K>
