@@ -609,7 +609,7 @@ bg_status bg_batch_create(bg_ctx_t ctx, const bg_tile* tiles, int n_tiles, bg_ba
     const size_t o_bsum = take(4 * (size_t)(scan_blocks(b->total_cells) + 1));
     const size_t o_acc = take(32 * (size_t)std::max(1, n_tiles));
     const size_t o_flags = take(16);
-    const size_t o_ctr = take(8 * 8);
+    const size_t o_ctr = take(8 * 16);  // [0] k-NN items, [1 + g] solve groups
     const size_t o_ids = take(4 * (size_t)b->total_ids);
     std::vector<size_t> o_gt, o_go;
     for (int q = 0; q < 4; ++q) {

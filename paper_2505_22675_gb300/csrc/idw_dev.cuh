@@ -33,7 +33,11 @@ __device__ __forceinline__ float idw_from(const HashView& h, int keff, float pow
     get(0, d0, i0);
     const float z1 = __int_as_float(__ldg(zb + 4 * (int64_t)i0));
     if (d0 == 0) return z1;  // node on top of a sounding
-    const float d1 = (float)d0;
+    // d2 as float: a 32-bit conversion when it fits (64-bit ones use the FP64 pipe)
+    auto d2f = [](uint64_t v) {
+        return v < (1ull << 31) ? __int2float_rn((int)v) : __ull2float_rn(v);
+    };
+    const float d1 = d2f(d0);
     const float l1 = log2f(d1);
     const float hp = 0.5f * power;
     float num = 0.0f, den = 1.0f;  // i = 0 contributes w = 1, anomaly 0
@@ -42,7 +46,7 @@ __device__ __forceinline__ float idw_from(const HashView& h, int keff, float pow
         int ii;
         get(i, di2, ii);
         const float zi = __int_as_float(__ldg(zb + 4 * (int64_t)ii));
-        const float di = (float)di2;
+        const float di = d2f(di2);
         const float w = (power == 2.0f) ? d1 / di : exp2f(hp * (l1 - log2f(di)));
         num = fmaf(w, zi - z1, num);
         den += w;

@@ -29,11 +29,14 @@ namespace bg {
 
 constexpr unsigned kFull = 0xffffffffu;
 
-// floor(off / cs) for 0 <= off < ncx*cs (exact: float estimate, integer fix-up)
+// floor(off / cs) for 0 <= off < ncx*cs (< 2^31; exact: float estimate, integer
+// fix-up). 32-bit conversions only: 64-bit int <-> float conversions run on
+// the FP64 pipe, a small fraction of the FP32 rate on this GPU.
 __device__ __forceinline__ int cell_of(const HashView& h, int64_t off) {
-    int c = (int)((float)off * h.inv_cs);
-    while ((int64_t)c * h.cs > off) --c;
-    while ((int64_t)(c + 1) * h.cs <= off) ++c;
+    const unsigned o = (unsigned)off, cs = (unsigned)h.cs;  // c * cs < 2^32 below
+    int c = max(0, __float2int_rz(__uint2float_rz(o) * h.inv_cs));
+    while ((unsigned)c * cs > o) --c;
+    while ((unsigned)(c + 1) * cs <= o) ++c;
     return c;
 }
 
@@ -44,8 +47,13 @@ __device__ __forceinline__ int clamp_cell(const HashView& h, int64_t off, int n)
     return cell_of(h, off);
 }
 
-// An upper bound on floor(sqrt(v)) for 0 <= v < 2^62.
+// An upper bound on floor(sqrt(v)) for 0 <= v < 2^62; 32-bit conversions
+// whenever v < 2^31 (the usual case: neighbour radii below ~460 m).
 __device__ __forceinline__ int64_t isqrt_ub(int64_t v) {
+    if (v < ((int64_t)1 << 31)) {
+        const float f = sqrtf(__int2float_ru((int)v));
+        return (int64_t)__float2int_ru(f * 1.0000020f) + 1;
+    }
     const float f = sqrtf((float)v);
     return (int64_t)(f * 1.0000020f) + 1;
 }
