@@ -343,4 +343,55 @@ __device__ __forceinline__ NodeIdx patch_node(int px, int py, int warp, int lane
     return NodeIdx{px * 16 + (warp & 1) * 8 + (lane & 7), py * 8 + (warp >> 1) * 4 + (lane >> 3)};
 }
 
+// ---------------------------------------------------------------------------
+// Strips: a thread grids kStrip consecutive nodes along x, one after another.
+// The first node's bound comes from the summed-area table. The next node is
+// one grid cell further along x, so its K-th distance is at most the
+// previous node's plus the cell (triangle inequality): a bound far tighter
+// than the table's square, which cuts the rows and candidates visited and the
+// heap inserts that are later evicted.
+constexpr int kStrip = 4;
+
+// Strip origin of this thread in the (16 * kStrip) x 8 node patch (px, py).
+__device__ __forceinline__ NodeIdx strip_origin(int px, int py, int warp, int lane) {
+    return NodeIdx{px * 16 * kStrip + (warp & 1) * 8 * kStrip + (lane & 7) * kStrip,
+                   py * 8 + (warp >> 1) * 4 + (lane >> 3)};
+}
+
+// Packed-key k-NN of nodes (i0 .. i0 + kStrip - 1, j) with the kc best in the
+// shared-memory heap hp (stride S). emit(i, cnt) runs after each node with its
+// keys sorted ascending in hp[0 .. cnt); a node whose table bound does not
+// fit the packed key is left to the wide pass (*flag = 1).
+template <int S, class Emit>
+__device__ __forceinline__ void knn_strip(const HashView& h, const GridView& g, int kc, int i0,
+                                          int j, uint64_t* hp, int* flag, Emit emit) {
+    const int qy = g.y0 + j * g.cell + g.cell / 2;
+    int64_t prev = -1;  // K-th squared distance of the previous node, -1 if none
+    int cy = 0;
+    for (int s = 0; s < kStrip; ++s) {
+        const int i = i0 + s;
+        if (i >= g.nx) break;
+        const int qx = g.x0 + i * g.cell + g.cell / 2;
+        Bound b{0, cy};
+        bool ok = false;
+        if (prev >= 0) {
+            const int64_t r = isqrt_ub(prev) + g.cell;  // >= ceil(d_K(prev)) + |step|
+            b.tau0 = r * r;
+            ok = packed_fits(h, b.tau0);
+        }
+        if (!ok) {
+            b = knn_bound_rt(h, qx, qy, kc);
+            cy = b.cy;
+            if (!packed_fits(h, b.tau0)) {
+                *flag = 1;
+                prev = -1;
+                continue;
+            }
+        }
+        const int cnt = knn_scan_heap_rt<S>(h, qx, qy, b, hp, kc);
+        prev = cnt == kc ? (int64_t)(hp[(kc - 1) * S] >> h.idx_bits) : -1;
+        emit(i, cnt);
+    }
+}
+
 }  // namespace bg
