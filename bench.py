@@ -58,6 +58,12 @@ def okrige_fp64_flops_per_node(k=OK_K):
     return 2 * n * n
 
 
+# DRAM bytes (read + write) per node of k_okrige_solve<32>, from one ncu
+# capture of the current kernel on the 2-line swath (3.384M nodes: 449.9 MB
+# read + 25.4 MB written per launch, mostly the 128 B of neighbour ids per
+# node); traffic grows with the nodes of a launch.
+SOLVE_DRAM_BYTES_PER_NODE = (449.854976e6 + 25.367552e6) / 3.384e6
+
 # FP32 peak for "alu"-bound roofline: 152 SMs x 128 FP32 lanes x 2 flops/FMA x
 # the maximum SM clock (2,070 MHz) = 80.5 TFLOP/s.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
@@ -412,6 +418,8 @@ def bench_ours(args):
         step(False)
     torch.cuda.synchronize()
     barrier()
+    bg.profile_read(ctx)  # discard anything recorded so far
+    bg.profile_enable(ctx, True)
     launches0 = bg.launch_count()
     start = torch.cuda.Event(enable_timing=True)
     stop = torch.cuda.Event(enable_timing=True)
@@ -423,6 +431,8 @@ def bench_ours(args):
         stop.record(stream)
         torch.cuda.synchronize()
     launches = bg.launch_count() - launches0
+    prof = bg.profile_read(ctx)
+    bg.profile_enable(ctx, False)
     barrier()
     ms = start.elapsed_time(stop) / args.steps
     stage = {k: statistics.median(a.elapsed_time(b) for a, b in v) for k, v in ev.items()}
@@ -466,9 +476,11 @@ def bench_ours(args):
 
     if rank == 0:
         peaks = load_peaks()
-        flops = okrige_flops_per_node() * m
-        ok_s = stage["ok"] / 1e3
-        achieved = flops / ok_s / 1e12
+        # dominant kernel: the kriging solve, timed per launch by events on its stream
+        s_ms, s_launch, s_nodes = prof["kriging_solve"]
+        solve_avg_ms = s_ms / max(s_launch, 1)
+        nodes_per_launch = s_nodes / max(s_launch, 1)
+        achieved = okrige_flops_per_node() * nodes_per_launch / (solve_avg_ms / 1e3) / 1e12
         clocks = clk.summary()
         out = {
             "metric": METRIC, "value": value, "unit": "nodes/s", "n_gpus": ws,
@@ -477,14 +489,18 @@ def bench_ours(args):
             "data": "synthetic", "config": config_dict(w, args),
             "stages_ms": {"hash_build": stage["hash"], "idw_k16": stage["idw"],
                           "kriging_k32": stage["ok"]},
+            "kernels_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
             "idw_nodes_per_s": m / (stage["idw"] / 1e3),
-            "kriging_nodes_per_s": m / ok_s,
-            "roofline": {"bound": "alu", "kernel": "k_okrige<32> (kNN + kriging k=32)",
+            "kriging_nodes_per_s": m / (stage["ok"] / 1e3),
+            "roofline": {"bound": "alu", "kernel": "k_okrige_solve<32> (kriging k=32 solve)",
                          "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                         "frac": achieved / FP32_PEAK_TFLOPS,
+                         "traffic": SOLVE_DRAM_BYTES_PER_NODE * nodes_per_launch,
+                         "avg_launch_ms": solve_avg_ms, "nodes_per_launch": nodes_per_launch,
                          "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
                          "flops_per_node": okrige_flops_per_node(),
-                         "fp64_flops_per_node": okrige_fp64_flops_per_node(),
+                         "traffic_source": "ncu dram bytes of the same kernel on a 3.384M-node "
+                                           "swath, scaled per node",
                          "hbm_peak_gbs_measured": peaks.get("hbm_gbs")},
             "e2e": {"value": ws * m / (e2e_ms / 1e3), "unit": "nodes/s",
                     "h2d_bytes_per_step": int(12 * w.x_cm.size),

@@ -140,9 +140,11 @@ bg_status bg_interp_idw(bg_soundings_t s, bg_grid_t grid, int k, float power,
 /* Local ordinary kriging over the k nearest valid soundings (Sec. III-C):
  * solves [Gamma 1; 1^T 0][lambda; mu] = [gamma_0; 1], returns
  * zhat = sum lambda_i z_i (Sec. III-C, estimate equation) and the kriging
- * variance sigma^2 = sum lambda_i gamma_i0 + mu. The system is solved in
- * FP32 with one step of iterative refinement whose residual is accumulated
- * in FP64; the weight sum is closed in FP64.
+ * variance sigma^2 = sum lambda_i gamma_i0 + mu. The system is reduced to a
+ * symmetric positive definite one (lambda_0 and mu eliminated), factored by
+ * Cholesky in FP32, and refined once: the residual b - A x is formed exactly
+ * (A as 30-bit and x as 24-bit fixed point, products summed in 64-bit
+ * integers, i.e. wider than FP64 would give). The weight sum closes in FP64.
  *   k in [1, 32]; v: variogram (see bg_variogram).
  *   depth_out, var_out: device, nx*ny float32 each (var_out may be NULL).
  *   nbr_out: as for bg_interp_idw.
@@ -287,6 +289,15 @@ const char* bg_version(void);
 /* Number of CUDA kernels this library has launched since it was loaded
  * (all threads, all contexts); a diagnostic for benchmarks. */
 bg_status bg_launch_count(uint64_t* out);
+
+/* Kernel timing for benchmarks. While enabled, the context records CUDA
+ * events on the launch stream around each interpolation kernel launch.
+ * bg_profile_read waits for the recorded events and returns, per stage
+ * (0 hash build, 1 IDW, 2 kriging k-NN ids, 3 kriging solve; n entries),
+ * the summed milliseconds, the launch count and the grid nodes processed,
+ * then clears the record. */
+bg_status bg_profile_enable(bg_ctx_t ctx, int on);
+bg_status bg_profile_read(bg_ctx_t ctx, double* ms, int64_t* launches, int64_t* units, int n);
 
 #ifdef __cplusplus
 }

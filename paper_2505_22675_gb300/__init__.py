@@ -25,7 +25,7 @@ OKRIGE = 1
 
 __all__ = [
     "BGError", "Variogram", "SoundingsInfo", "SPHERICAL", "EXPONENTIAL", "IDW", "OKRIGE",
-    "version", "launch_count", "ctx_create", "ctx_destroy", "ctx_device_bytes", "grid_create", "grid_destroy",
+    "version", "launch_count", "profile_enable", "profile_read", "ctx_create", "ctx_destroy", "ctx_device_bytes", "grid_create", "grid_destroy",
     "soundings_upload", "soundings_info", "soundings_destroy", "interp_idw", "interp_okrige",
     "variogram", "interp_idw_noalloc", "submit", "poll", "wait", "cancel", "serve_stats",
     "serve_shutdown", "Request", "Result", "Batch", "batch_create", "batch_run", "batch_tune",
@@ -73,6 +73,24 @@ def launch_count() -> int:
     out = ctypes.c_uint64()
     check(_lib().bg_launch_count(ctypes.byref(out)), "bg_launch_count")
     return out.value
+
+
+PROFILE_STAGES = ("hash_build", "idw", "kriging_knn_ids", "kriging_solve")
+
+
+def profile_enable(ctx, on: bool = True) -> None:
+    """Record CUDA events around each interpolation kernel launch of ctx."""
+    check(_lib().bg_profile_enable(ctx, int(bool(on))), "bg_profile_enable")
+
+
+def profile_read(ctx) -> dict:
+    """{stage: (total ms, launches, grid nodes)} since the last read; clears."""
+    n = len(PROFILE_STAGES)
+    ms = (ctypes.c_double * n)()
+    la = (ctypes.c_int64 * n)()
+    un = (ctypes.c_int64 * n)()
+    check(_lib().bg_profile_read(ctx, ms, la, un, n), "bg_profile_read")
+    return {name: (ms[i], la[i], un[i]) for i, name in enumerate(PROFILE_STAGES)}
 
 
 def variogram(model: int = SPHERICAL, nugget_m2: float = 0.25, sill_m2: float = 100.0,

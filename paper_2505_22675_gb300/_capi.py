@@ -71,6 +71,9 @@ _SIGNATURES = {
     "bg_last_error": ([], ctypes.c_char_p),
     "bg_status_str": ([ctypes.c_int], ctypes.c_char_p),
     "bg_launch_count": ([ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
+    "bg_profile_enable": ([P, ctypes.c_int], ctypes.c_int),
+    "bg_profile_read": ([P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
+                         ctypes.POINTER(ctypes.c_int64), ctypes.c_int], ctypes.c_int),
     "bg_ctx_create": ([ctypes.c_int, ctypes.c_size_t, PP], ctypes.c_int),
     "bg_ctx_destroy": ([P], ctypes.c_int),
     "bg_ctx_device_bytes": ([P, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),

@@ -7,6 +7,7 @@
 #include <atomic>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "bathygrid.h"
 
@@ -63,8 +64,25 @@ struct Server;  // serving state of a context (serve.cu)
 
 }  // namespace bg
 
+// Per-context kernel timing (bg_profile_*): CUDA events recorded on the
+// launch stream around each timed kernel, read back on request.
+namespace bg {
+struct ProfEntry {
+    int stage;
+    int64_t units;
+    cudaEvent_t a, b;
+};
+struct Profiler {
+    bool on = false;
+    std::mutex mu;
+    std::vector<ProfEntry> live;        // recorded, not yet read
+    std::vector<cudaEvent_t> spare;     // reusable events
+};
+}  // namespace bg
+
 struct bg_ctx_s {
     int device = 0;
+    bg::Profiler prof;
     size_t budget = 0;                 // 0 = unlimited
     std::atomic<int64_t> in_use{0};
     std::mutex mu;
@@ -92,6 +110,20 @@ struct bg_soundings_s {
 };
 
 namespace bg {
+
+// Stage ids of the profiler.
+enum ProfStage { kProfHash = 0, kProfIdw = 1, kProfKnnIds = 2, kProfSolve = 3, kProfStages = 4 };
+
+// Scope that records events around the work it encloses when profiling is on.
+struct ProfScope {
+    bg_ctx_s* ctx;
+    int stage;
+    int64_t units;
+    cudaStream_t st;
+    cudaEvent_t a = nullptr, b = nullptr;
+    ProfScope(bg_ctx_s* c, int stage_id, int64_t work_units, cudaStream_t s);
+    ~ProfScope();
+};
 
 // Budgeted stream-ordered allocation (cudaMallocAsync) charged to a context.
 bg_status dalloc(bg_ctx_s* ctx, void** p, size_t bytes, cudaStream_t st);

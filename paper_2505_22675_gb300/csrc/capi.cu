@@ -82,6 +82,33 @@ void free_soundings(bg_soundings_s* s, cudaStream_t st) {
     s->d_orig = s->d_cell_start = s->d_sat = s->d_rec = nullptr;
 }
 
+static cudaEvent_t take_event(Profiler& pr) {
+    cudaEvent_t e = nullptr;
+    if (!pr.spare.empty()) {
+        e = pr.spare.back();
+        pr.spare.pop_back();
+    } else if (cudaEventCreate(&e) != cudaSuccess) {
+        e = nullptr;
+    }
+    return e;
+}
+
+ProfScope::ProfScope(bg_ctx_s* c, int stage_id, int64_t work_units, cudaStream_t s)
+    : ctx(c), stage(stage_id), units(work_units), st(s) {
+    if (!ctx || !ctx->prof.on) return;
+    std::lock_guard<std::mutex> lk(ctx->prof.mu);
+    a = take_event(ctx->prof);
+    b = take_event(ctx->prof);
+    if (a) cudaEventRecord(a, st);
+}
+
+ProfScope::~ProfScope() {
+    if (!a || !b) return;
+    cudaEventRecord(b, st);
+    std::lock_guard<std::mutex> lk(ctx->prof.mu);
+    ctx->prof.live.push_back(ProfEntry{stage, units, a, b});
+}
+
 size_t soundings_bytes_estimate(int64_t n, int64_t n_valid) {
     // records (2 x 16 B), cell tables (~2 soundings per cell: cell_start + SAT
     // + counts), host staging (12 B), small scratch
@@ -161,6 +188,37 @@ bg_status bg_ctx_create(int device, size_t hbm_budget_bytes, bg_ctx_t* out) {
     return BG_OK;
 }
 
+bg_status bg_profile_enable(bg_ctx_t ctx, int on) {
+    BG_REQUIRE(ctx, "ctx is NULL");
+    std::lock_guard<std::mutex> lk(ctx->prof.mu);
+    ctx->prof.on = on != 0;
+    return BG_OK;
+}
+
+bg_status bg_profile_read(bg_ctx_t ctx, double* ms, int64_t* launches, int64_t* units, int n) {
+    BG_REQUIRE(ctx && ms && launches && units && n > 0, "bad arguments");
+    for (int i = 0; i < n; ++i) {
+        ms[i] = 0.0;
+        launches[i] = 0;
+        units[i] = 0;
+    }
+    std::lock_guard<std::mutex> lk(ctx->prof.mu);
+    for (const auto& e : ctx->prof.live) {
+        cudaEventSynchronize(e.b);
+        float t = 0.0f;
+        cudaEventElapsedTime(&t, e.a, e.b);
+        if (e.stage >= 0 && e.stage < n) {
+            ms[e.stage] += t;
+            launches[e.stage] += 1;
+            units[e.stage] += e.units;
+        }
+        ctx->prof.spare.push_back(e.a);
+        ctx->prof.spare.push_back(e.b);
+    }
+    ctx->prof.live.clear();
+    return BG_OK;
+}
+
 bg_status bg_ctx_device_bytes(bg_ctx_t ctx, int64_t* out) {
     BG_REQUIRE(ctx && out, "NULL argument");
     *out = ctx->in_use.load();
@@ -174,6 +232,11 @@ bg_status bg_ctx_destroy(bg_ctx_t ctx) {
     DeviceGuard dg(ctx->device);
     bg_serve_shutdown(ctx);
     cudaDeviceSynchronize();
+    for (auto& e : ctx->prof.live) {
+        cudaEventDestroy(e.a);
+        cudaEventDestroy(e.b);
+    }
+    for (auto e : ctx->prof.spare) cudaEventDestroy(e);
     cudaFreeHost(ctx->h_pinned);
     cudaMemPoolDestroy(ctx->pool);
     delete ctx;

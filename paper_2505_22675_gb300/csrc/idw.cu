@@ -61,11 +61,14 @@ __global__ void __launch_bounds__(128) k_idw_wide(HashView h, GridView g, int k,
 
 template <int K>
 bg_status launch_k(const HashView& h, const GridView& g, int k, float power, float* depth,
-                   int32_t* nbr, int* d_flag, cudaStream_t st) {
+                   int32_t* nbr, int* d_flag, cudaStream_t st, bg_ctx_s* prof_ctx) {
     const int64_t nb = (int64_t)((g.nx + 15) / 16) * ((g.ny + 7) / 8);
     const int64_t nbs = (int64_t)((g.nx + 16 * kStrip - 1) / (16 * kStrip)) * ((g.ny + 7) / 8);
     BG_CUDA(cudaMemsetAsync(d_flag, 0, sizeof(int), st));
-    k_idw<K><<<(unsigned)nbs, 128, 0, st>>>(h, g, k, power, depth, nbr, d_flag);
+    {
+        ProfScope ps(prof_ctx, kProfIdw, (int64_t)g.nx * g.ny, st);
+        k_idw<K><<<(unsigned)nbs, 128, 0, st>>>(h, g, k, power, depth, nbr, d_flag);
+    }
     k_idw_wide<K><<<(unsigned)std::min<int64_t>(nb, 152 * 4), 128, 0, st>>>(h, g, k, power, depth,
                                                                         nbr, d_flag);
     note_launches(2);
@@ -84,10 +87,10 @@ bg_status launch_idw(const bg_soundings_s* s, const GridView& g, int k, float po
     bg_status rc = dalloc(s->ctx, (void**)&flag, sizeof(int), st);
     if (rc != BG_OK) return rc;
     switch (K) {
-        case 4: rc = launch_k<4>(h, g, k, power, depth, nbr, flag, st); break;
-        case 8: rc = launch_k<8>(h, g, k, power, depth, nbr, flag, st); break;
-        case 16: rc = launch_k<16>(h, g, k, power, depth, nbr, flag, st); break;
-        default: rc = launch_k<32>(h, g, k, power, depth, nbr, flag, st); break;
+        case 4: rc = launch_k<4>(h, g, k, power, depth, nbr, flag, st, s->ctx); break;
+        case 8: rc = launch_k<8>(h, g, k, power, depth, nbr, flag, st, s->ctx); break;
+        case 16: rc = launch_k<16>(h, g, k, power, depth, nbr, flag, st, s->ctx); break;
+        default: rc = launch_k<32>(h, g, k, power, depth, nbr, flag, st, s->ctx); break;
     }
     dfree(s->ctx, flag, sizeof(int), st);
     return rc;
@@ -99,10 +102,10 @@ bg_status launch_idw_with_flag(const bg_soundings_s* s, const GridView& g, int k
     const int K = k <= 4 ? 4 : k <= 8 ? 8 : k <= 16 ? 16 : 32;
     h.r0 = start_halfwidth(s, K);
     switch (K) {
-        case 4: return launch_k<4>(h, g, k, power, depth, nbr, d_flag, st);
-        case 8: return launch_k<8>(h, g, k, power, depth, nbr, d_flag, st);
-        case 16: return launch_k<16>(h, g, k, power, depth, nbr, d_flag, st);
-        default: return launch_k<32>(h, g, k, power, depth, nbr, d_flag, st);
+        case 4: return launch_k<4>(h, g, k, power, depth, nbr, d_flag, st, s->ctx);
+        case 8: return launch_k<8>(h, g, k, power, depth, nbr, d_flag, st, s->ctx);
+        case 16: return launch_k<16>(h, g, k, power, depth, nbr, d_flag, st, s->ctx);
+        default: return launch_k<32>(h, g, k, power, depth, nbr, d_flag, st, s->ctx);
     }
 }
 

@@ -80,13 +80,19 @@ bg_status launch_k(const HashView& h, const GridView& g, int k, const OkParams& 
             rc = cuda_fail(e, "memset");
             break;
         }
-        k_knn_ids<K><<<(unsigned)nbs, 128, 0, st>>>(h, g, k, (int)j0, (int)j1, chunk_ids, flag);
+        const int64_t nodes = (j1 - j0) * g.nx;
+        {
+            ProfScope ps(ctx, kProfKnnIds, nodes, st);
+            k_knn_ids<K><<<(unsigned)nbs, 128, 0, st>>>(h, g, k, (int)j0, (int)j1, chunk_ids, flag);
+        }
         k_knn_ids_wide<K><<<(unsigned)std::min<int64_t>(nb, 152 * 4), 128, 0, st>>>(
             h, g, k, (int)j0, (int)j1, chunk_ids, flag);
-        const int64_t nodes = (j1 - j0) * g.nx;
         const int64_t sb = (nodes + sys_per_block - 1) / sys_per_block;
-        k_okrige_solve<K><<<(unsigned)sb, kSolveWarps * 32, 0, st>>>(h, g, k, p, j0 * g.nx, nodes,
-                                                                     chunk_ids, depth, var);
+        {
+            ProfScope ps(ctx, kProfSolve, nodes, st);
+            k_okrige_solve<K><<<(unsigned)sb, kSolveWarps * 32, 0, st>>>(h, g, k, p, j0 * g.nx, nodes,
+                                                                         chunk_ids, depth, var);
+        }
         note_launches(3);
         e = cudaGetLastError();
         if (e != cudaSuccess) {

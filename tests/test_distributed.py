@@ -1,0 +1,125 @@
+"""Multi-GPU partitioning logic, run as CPU ranks over gloo (world size 2).
+
+The per-rank compute is the FP64 oracle here, so the test checks only the
+partitioning, the broadcast of the soundings and the gather of the slabs or
+tiles: the assembled grids must equal the oracle's single-process grids.
+"""
+import os
+import socket
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from paper_2505_22675_gb300 import distributed as D
+
+
+def oracle_compute(x, y, z, spec, method, k, power, vgm):
+    qx, qy = oracle.grid_nodes(*spec)
+    if method == D.IDW:
+        return oracle.idw(x, y, z, qx, qy, k, power, nthreads=1).astype(np.float32), None
+    d, v = oracle.okrige(x, y, z, qx, qy, k, *vgm, nthreads=1)
+    return d.astype(np.float32), v.astype(np.float32)
+
+
+def test_slab_rows_cover_the_grid():
+    for ny in (1, 7, 100, 3692):
+        for world in (1, 2, 3, 8):
+            rows = [D.slab_rows(ny, world, r) for r in range(world)]
+            assert rows[0][0] == 0 and rows[-1][1] == ny
+            assert all(a[1] == b[0] for a, b in zip(rows, rows[1:]))
+            sizes = [b - a for a, b in rows]
+            assert max(sizes) - min(sizes) <= 1
+    assert D.slab_spec((100, 200, 50, 10, 20), 5, 12) == (100, 450, 50, 10, 7)
+
+
+def test_assign_tiles_balances_and_is_deterministic():
+    rng = np.random.default_rng(0)
+    costs = list(rng.lognormal(10, 1, 200))
+    a = D.assign_tiles(costs, 4)
+    assert a == D.assign_tiles(costs, 4)
+    loads = np.zeros(4)
+    for c, r in zip(costs, a):
+        loads[r] += c
+    assert loads.max() - loads.min() <= max(costs)  # LPT bound
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _rank_main(rank, world, port, out_dir):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        w = synth.swath(seed=2, lines=2, pings=40, beams=32)
+        g = w.grid
+        spec = (g.x0_cm, g.y0_cm, g.cell_cm, g.nx, g.ny)
+        src = (w.x_cm, w.y_cm, w.z_m) if rank == 0 else (None, None, None)
+        d, _ = D.grid_swath(*src, spec, D.IDW, 8, compute=oracle_compute)
+        dk, vk = D.grid_swath(*src, spec, D.OKRIGE, 8, compute=oracle_compute)
+        tiles = []
+        for t, (tw, m) in enumerate(synth.batched_tiles(seed=4, count=7, scale=0.005)):
+            tg = tw.grid
+            tiles.append(dict(x_cm=tw.x_cm, y_cm=tw.y_cm, z_m=tw.z_m, method=m, k=8,
+                              grid_spec=(tg.x0_cm, tg.y0_cm, tg.cell_cm, tg.nx, tg.ny)))
+        res = D.grid_tiles(tiles, compute=oracle_compute)
+        if rank == 0:
+            np.save(os.path.join(out_dir, "idw.npy"), d)
+            np.save(os.path.join(out_dir, "okd.npy"), dk)
+            np.save(os.path.join(out_dir, "okv.npy"), vk)
+            for i, (td, tv) in enumerate(res):
+                np.save(os.path.join(out_dir, f"tile{i}_d.npy"), td)
+                if tv is not None:
+                    np.save(os.path.join(out_dir, f"tile{i}_v.npy"), tv)
+        else:
+            assert d is None and res is None
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_match_single_process(tmp_path):
+    import torch.multiprocessing as mp
+    mp.spawn(_rank_main, args=(2, _free_port(), str(tmp_path)), nprocs=2, join=True)
+    w = synth.swath(seed=2, lines=2, pings=40, beams=32)
+    g = w.grid
+    spec = (g.x0_cm, g.y0_cm, g.cell_cm, g.nx, g.ny)
+    d, _ = oracle_compute(w.x_cm, w.y_cm, w.z_m, spec, D.IDW, 8, 2.0, None)
+    assert np.array_equal(np.load(tmp_path / "idw.npy"), d)
+    dk, vk = oracle_compute(w.x_cm, w.y_cm, w.z_m, spec, D.OKRIGE, 8, 2.0, (0, 0.25, 100.0, 50.0))
+    assert np.array_equal(np.load(tmp_path / "okd.npy"), dk)
+    assert np.array_equal(np.load(tmp_path / "okv.npy"), vk)
+    for i, (tw, m) in enumerate(synth.batched_tiles(seed=4, count=7, scale=0.005)):
+        tg = tw.grid
+        rd, rv = oracle_compute(tw.x_cm, tw.y_cm, tw.z_m, (tg.x0_cm, tg.y0_cm, tg.cell_cm, tg.nx, tg.ny),
+                                m, 8, 2.0, (0, 0.25, 100.0, 50.0))
+        assert np.array_equal(np.load(tmp_path / f"tile{i}_d.npy"), rd)
+        if m == D.OKRIGE:
+            assert np.array_equal(np.load(tmp_path / f"tile{i}_v.npy"), rv)
+
+
+@pytest.mark.gpu
+def test_slabs_on_one_gpu_equal_the_unsplit_grid():
+    """The slabs a multi-GPU run would compute, run one after another on one
+    GPU, assemble into exactly the single-GPU grid."""
+    w = synth.swath(seed=2, lines=2, pings=300, beams=256)
+    g = w.grid
+    spec = (g.x0_cm, g.y0_cm, g.cell_cm, g.nx, g.ny)
+    run = D.library_compute(0)
+    for method, k in ((D.IDW, 16), (D.OKRIGE, 32)):
+        full_d, full_v = run(w.x_cm, w.y_cm, w.z_m, spec, method, k, 2.0, (0, 0.25, 100.0, 50.0))
+        for world in (2, 3):
+            parts = [run(w.x_cm, w.y_cm, w.z_m, D.slab_spec(spec, *D.slab_rows(g.ny, world, r)),
+                         method, k, 2.0, (0, 0.25, 100.0, 50.0)) for r in range(world)]
+            d = np.concatenate([p[0] for p in parts])
+            assert np.array_equal(d.view(np.uint32), full_d.view(np.uint32))
+            if method == D.OKRIGE:
+                v = np.concatenate([p[1] for p in parts])
+                assert np.array_equal(v.view(np.uint32), full_v.view(np.uint32))
