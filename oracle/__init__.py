@@ -1,4 +1,5 @@
-"""FP64 CPU oracle for exact k-NN, IDW and ordinary kriging (ctypes over oracle.c).
+"""FP64 CPU oracle for exact k-NN, IDW, ordinary kriging and gridded
+bilinear / Catmull-Rom resampling (ctypes over oracle.c).
 
 TEST INFRASTRUCTURE ONLY: the test suite, the smoke check and the CPU-baseline
 leg of the benchmark may import this package; the library under
@@ -57,6 +58,8 @@ def _load():
     lib.oracle_variogram.restype = dbl
     lib.oracle_solve.argtypes = [ctypes.c_int, P, P, P]
     lib.oracle_solve.restype = ctypes.c_int
+    lib.oracle_resample.argtypes = [P, i32, i32, i32, i32, i32, ctypes.c_int, P, P, i64, P, P]
+    lib.oracle_resample.restype = ctypes.c_int
     lib.oracle_threads.argtypes = [ctypes.c_int]
     lib.oracle_threads.restype = ctypes.c_int
     _lib = lib
@@ -156,3 +159,30 @@ def solve(A, b):
     if _load().oracle_solve(n, _p(A), _p(b), _p(x)) != 0:
         raise np.linalg.LinAlgError("zero pivot")
     return x
+
+
+BILINEAR = 0
+CATMULL_ROM = 1
+
+
+def resample(src, grid_spec, qx, qy, method: int):
+    """Bilinear (method 0) or Catmull-Rom (1) of a regular grid at query points.
+
+    src: float32 [ny * nx] row-major node values (NaN = missing); grid_spec =
+    (x0_cm, y0_cm, cell_cm, nx, ny). Returns (values float64[m], how int8[m]):
+    how = 0 by the method itself, 1 by the bilinear fallback, 2 no value (NaN).
+    """
+    x0, y0, cell, nx, ny = (int(v) for v in grid_spec)
+    src = np.ascontiguousarray(src, dtype=np.float32)
+    if src.size != nx * ny:
+        raise ValueError("src must hold nx * ny values")
+    qx = np.ascontiguousarray(qx, dtype=np.int32)
+    qy = np.ascontiguousarray(qy, dtype=np.int32)
+    m = qx.size
+    out = np.empty(m, dtype=np.float64)
+    how = np.empty(m, dtype=np.int8)
+    rc = _load().oracle_resample(_p(src), x0, y0, cell, nx, ny, int(method), _p(qx), _p(qy), m,
+                                 _p(out), _p(how))
+    if rc != 0:
+        raise ValueError("oracle_resample: bad arguments")
+    return out, how

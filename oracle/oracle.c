@@ -28,6 +28,20 @@
  *     the printed matrix equation of Sec. III-C omits;
  *   - fewer valid soundings than k: k_eff = min(k, N_valid); none gives NaN.
  *
+ *
+ * Gridded input (the paper's own stencil methods, Sec. III-A and III-B):
+ *   - bilinear interpolation of a regular grid at a query point from the
+ *     four nodes of the cell that holds it (Sec. III-A, the formula with
+ *     (x2 - x)(y2 - y) Q11 + ... over (x2 - x1)(y2 - y1));
+ *   - Catmull-Rom: the 4 x 4 nodes around that cell, the cubic C(t) of
+ *     Sec. III-B applied along x on each of the 4 rows, then along y.
+ *   Readings: a node is needed when its weight is not zero (a query on a
+ *   node line needs only that line); a needed NaN node makes bilinear NaN
+ *   (it has no fallback, Sec. III-D) and sends Catmull-Rom to bilinear
+ *   (Sec. III-B, read as "if not enough valid neighbours"); stencil indices
+ *   past the grid edge repeat the edge node; a query outside the hull of
+ *   the node centres gets NaN.
+ *
  * Build: gcc -O2 -std=c11 -shared -fPIC -pthread oracle.c -o liboracle.so -lm
  * (no -ffast-math: the NaN tests and the rounding of every step must be IEEE).
  */
@@ -379,6 +393,119 @@ int oracle_okrige(const int32_t* x, const int32_t* y, const float* z, int64_t n,
     ok_args a = {x, y, z, n, qx, qy, k, model, nugget, sill, range_m,
                  depth_out, var_out, lambda_out, mu_out, idx_out};
     parallel_for(m, nthreads, ok_range, &a);
+    return 0;
+}
+
+/* ------------------------------------------------------ gridded input */
+
+/* The cell of the node lattice that holds query offset u (cm from the first
+ * node centre) along an axis of n nodes at spacing cell: index i in
+ * [0, n - 2] and remainder r in [0, cell] with u = i * cell + r; -1 outside. */
+static int lattice_cell(int64_t u, int64_t cell, int n, int64_t* r) {
+    if (u < 0 || u > (int64_t)(n - 1) * cell) return -1;
+    int64_t i = u / cell;
+    if (i > n - 2) i = n - 2;
+    *r = u - i * cell;
+    return (int)i;
+}
+
+/* Bilinear (Sec. III-A) at (qx, qy): Q11, Q21, Q12, Q22 are the nodes at
+ * (x1, y1), (x2, y1), (x1, y2), (x2, y2). Returns NaN when a node whose
+ * weight is not zero is NaN, or outside the hull. */
+static double bilinear_one(const float* v, int64_t x0, int64_t y0, int64_t cell, int nx, int ny,
+                           int64_t qx, int64_t qy) {
+    int64_t rx, ry;
+    const int i = lattice_cell(qx - (x0 + cell / 2), cell, nx, &rx);
+    const int j = lattice_cell(qy - (y0 + cell / 2), cell, ny, &ry);
+    if (i < 0 || j < 0) return NAN;
+    const double x1 = (double)(x0 + cell / 2 + (int64_t)i * cell), x2 = x1 + (double)cell;
+    const double y1 = (double)(y0 + cell / 2 + (int64_t)j * cell), y2 = y1 + (double)cell;
+    const double x = (double)qx, y = (double)qy;
+    const double q11 = v[(int64_t)j * nx + i], q21 = v[(int64_t)j * nx + i + 1];
+    const double q12 = v[(int64_t)(j + 1) * nx + i], q22 = v[(int64_t)(j + 1) * nx + i + 1];
+    const double w11 = (x2 - x) * (y2 - y), w21 = (x - x1) * (y2 - y);
+    const double w12 = (x2 - x) * (y - y1), w22 = (x - x1) * (y - y1);
+    const double q[4] = {q11, q21, q12, q22}, w[4] = {w11, w21, w12, w22};
+    double acc = 0.0;
+    for (int c = 0; c < 4; ++c) {
+        if (w[c] == 0.0) continue;  /* not needed */
+        if (isnan(q[c])) return NAN;
+        acc += w[c] * q[c];
+    }
+    return acc / ((x2 - x1) * (y2 - y1));
+}
+
+/* The Catmull-Rom cubic of Sec. III-B through P1 (t = 0) and P2 (t = 1). */
+static double catmull_rom_1d(double p0, double p1, double p2, double p3, double t) {
+    return 0.5 * (2.0 * p1 + (-p0 + p2) * t + (2.0 * p0 - 5.0 * p1 + 4.0 * p2 - p3) * t * t +
+                  (-p0 + 3.0 * p1 - 3.0 * p2 + p3) * t * t * t);
+}
+
+/* Which of P0..P3 carry weight at t: all four inside the cell, only P1 at
+ * t = 0, only P2 at t = 1 (the cubic's weights vanish nowhere else in [0, 1]). */
+static void cr_needed(int64_t r, int64_t cell, int need[4]) {
+    for (int a = 0; a < 4; ++a) need[a] = (r == 0) ? (a == 1) : (r == cell) ? (a == 2) : 1;
+}
+
+static int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+/* Catmull-Rom at (qx, qy); *how = 0 cubic, 1 bilinear fallback, 2 no value. */
+static double catmull_rom_one(const float* v, int64_t x0, int64_t y0, int64_t cell, int nx,
+                              int ny, int64_t qx, int64_t qy, int8_t* how) {
+    int64_t rx, ry;
+    const int i = lattice_cell(qx - (x0 + cell / 2), cell, nx, &rx);
+    const int j = lattice_cell(qy - (y0 + cell / 2), cell, ny, &ry);
+    if (i < 0 || j < 0) {
+        *how = 2;
+        return NAN;
+    }
+    int nxd[4], nyd[4];
+    cr_needed(rx, cell, nxd);
+    cr_needed(ry, cell, nyd);
+    double P[4][4];  /* P[b][a]: row j - 1 + b, column i - 1 + a (edges repeated) */
+    int ok = 1;
+    for (int b = 0; b < 4; ++b)
+        for (int a = 0; a < 4; ++a) {
+            const int ii = clampi(i - 1 + a, 0, nx - 1), jj = clampi(j - 1 + b, 0, ny - 1);
+            const double val = v[(int64_t)jj * nx + ii];
+            if (nxd[a] && nyd[b]) {
+                if (isnan(val)) ok = 0;
+                P[b][a] = val;
+            } else {
+                P[b][a] = 0.0;  /* weight zero: the value does not enter */
+            }
+        }
+    if (!ok) {
+        const double f = bilinear_one(v, x0, y0, cell, nx, ny, qx, qy);
+        *how = isnan(f) ? 2 : 1;
+        return f;
+    }
+    const double t = (double)rx / (double)cell, s = (double)ry / (double)cell;
+    double row[4];
+    for (int b = 0; b < 4; ++b) row[b] = catmull_rom_1d(P[b][0], P[b][1], P[b][2], P[b][3], t);
+    *how = 0;
+    return catmull_rom_1d(row[0], row[1], row[2], row[3], s);
+}
+
+/* method 0 = bilinear, 1 = Catmull-Rom; how may be NULL. */
+int oracle_resample(const float* v, int32_t x0, int32_t y0, int32_t cell, int32_t nx, int32_t ny,
+                    int method, const int32_t* qx, const int32_t* qy, int64_t m, double* out,
+                    int8_t* how) {
+    if (!v || cell <= 0 || nx < 2 || ny < 2 || m < 0 || (m > 0 && (!qx || !qy || !out)) ||
+        (method != 0 && method != 1))
+        return -1;
+    for (int64_t p = 0; p < m; ++p) {
+        int8_t h = 0;
+        double f;
+        if (method == 0) {
+            f = bilinear_one(v, x0, y0, cell, nx, ny, qx[p], qy[p]);
+            h = isnan(f) ? 2 : 0;
+        } else {
+            f = catmull_rom_one(v, x0, y0, cell, nx, ny, qx[p], qy[p], &h);
+        }
+        out[p] = f;
+        if (how) how[p] = h;
+    }
     return 0;
 }
 

@@ -366,3 +366,118 @@ def test_okrige_exchangeable_with_constant_field():
 def test_okrige_no_valid_soundings_is_nan():
     d, v = oracle.okrige([0, 1], [0, 1], [np.nan, np.nan], [0], [0], 4)
     assert math.isnan(d[0]) and math.isnan(v[0])
+
+
+# ------------------------------------------------------- gridded input
+
+RESAMPLE_GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "resample_hand_worked.txt")
+
+
+def _resample_golden():
+    cases = []
+    with open(RESAMPLE_GOLDEN) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            name, size, vals, q, method, expected, how = [s.strip() for s in line.split("|")]
+            nx, ny = (int(v) for v in size.split())
+            values = np.array([float(v) for v in vals.split(",")], dtype=np.float32)
+            qx, qy = (int(v) for v in q.split())
+            if expected == "nan":
+                exp = math.nan
+            else:
+                num, den = expected.split("/")
+                exp = float(num) / float(den)
+            cases.append((name, nx, ny, values, qx, qy, int(method), exp, int(how)))
+    return cases
+
+
+@pytest.mark.parametrize("case", _resample_golden(), ids=lambda c: c[0])
+def test_resample_hand_worked(case):
+    name, nx, ny, values, qx, qy, method, exp, how = case
+    out, h = oracle.resample(values, (0, 0, 200, nx, ny), [qx], [qy], method)
+    if math.isnan(exp):
+        assert math.isnan(out[0])
+    else:
+        assert out[0] == pytest.approx(exp, abs=1e-12)
+    assert h[0] == how
+
+
+def _node_values(nx, ny, cell, f, x0=0, y0=0):
+    """Node values f(x_m, y_m) on the lattice, row-major."""
+    xs = (x0 + np.arange(nx) * cell + cell // 2) / 100.0
+    ys = (y0 + np.arange(ny) * cell + cell // 2) / 100.0
+    X, Y = np.meshgrid(xs, ys)
+    return f(X, Y).astype(np.float64).ravel()
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_bilinear_reproduces_bilinear_functions(seed):
+    rng = np.random.default_rng(seed)
+    nx, ny, cell = int(rng.integers(2, 9)), int(rng.integers(2, 9)), 2 * int(rng.integers(1, 200))
+    a, b, c, d = rng.normal(size=4)
+    f = lambda x, y: a + b * x + c * y + d * x * y  # noqa: E731
+    src = _node_values(nx, ny, cell, f).astype(np.float32)
+    # float32 nodes: compare with the function of the rounded nodes, i.e. the
+    # bilinear interpolant of src itself, through exact corners only
+    qx = rng.integers(cell // 2, cell // 2 + (nx - 1) * cell + 1, 400)
+    qy = rng.integers(cell // 2, cell // 2 + (ny - 1) * cell + 1, 400)
+    got, how = oracle.resample(src, (0, 0, cell, nx, ny), qx, qy, oracle.BILINEAR)
+    exact = _node_values(nx, ny, cell, f)  # unrounded corner values
+    ref = f(qx / 100.0, qy / 100.0)
+    # rounding of the nodes to float32 moves a convex combination by at most their ulp
+    assert np.all(how == 0)
+    assert np.max(np.abs(got - ref)) <= 2 * np.max(np.abs(exact - src)) + 1e-12
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_catmull_rom_reproduces_separable_quadratics(seed):
+    rng = np.random.default_rng(10 + seed)
+    nx, ny, cell = 9, 8, 200
+    p = rng.normal(size=3)
+    q = rng.normal(size=3)
+    f = lambda x, y: (p[0] + p[1] * x + p[2] * x * x) * (q[0] + q[1] * y + q[2] * y * y)  # noqa: E731
+    src64 = _node_values(nx, ny, cell, f)
+    src = src64.astype(np.float32)
+    # interior cells only (the 4 x 4 stencil does not reach the edge)
+    qx = rng.integers(100 + 200, 100 + 200 * (nx - 2) + 1, 300)
+    qy = rng.integers(100 + 200, 100 + 200 * (ny - 2) + 1, 300)
+    got, how = oracle.resample(src, (0, 0, cell, nx, ny), qx, qy, oracle.CATMULL_ROM)
+    assert np.all(how == 0)
+    # Catmull-Rom weights are bounded (sum |w| <= 1.25 per axis): node rounding moves
+    # the result by at most 1.25^2 * the largest node rounding error
+    bound = 1.25 ** 2 * np.max(np.abs(src64 - src)) + 1e-9
+    assert np.max(np.abs(got - f(qx / 100.0, qy / 100.0))) <= bound
+
+
+def test_gridded_methods_at_nodes_outside_and_last_node():
+    nx, ny, cell = 5, 4, 200
+    rng = np.random.default_rng(3)
+    src = rng.normal(3500, 20, nx * ny).astype(np.float32)
+    i, j = np.meshgrid(np.arange(nx), np.arange(ny))
+    qx = (100 + 200 * i).ravel()
+    qy = (100 + 200 * j).ravel()
+    for method in (oracle.BILINEAR, oracle.CATMULL_ROM):
+        got, how = oracle.resample(src, (0, 0, cell, nx, ny), qx, qy, method)
+        assert np.array_equal(got, src.astype(np.float64)) and np.all(how == 0)
+        out, how = oracle.resample(src, (0, 0, cell, nx, ny), [99, 100, 901, 500], [100, 99, 100, 701],
+                                   method)
+        assert np.isnan(out).all() and np.all(how == 2)
+
+
+def test_catmull_rom_falls_back_exactly_to_bilinear():
+    nx, ny, cell = 12, 10, 200
+    rng = np.random.default_rng(4)
+    src = rng.normal(3500, 20, nx * ny).astype(np.float32)
+    src[rng.choice(nx * ny, 12, replace=False)] = np.nan
+    qx = rng.integers(100, 100 + 200 * (nx - 1) + 1, 3000)
+    qy = rng.integers(100, 100 + 200 * (ny - 1) + 1, 3000)
+    cr, how = oracle.resample(src, (0, 0, cell, nx, ny), qx, qy, oracle.CATMULL_ROM)
+    bl, bhow = oracle.resample(src, (0, 0, cell, nx, ny), qx, qy, oracle.BILINEAR)
+    assert set(np.unique(how)) == {0, 1, 2}
+    fb = how >= 1
+    assert np.array_equal(np.isnan(cr[fb]), np.isnan(bl[fb]))
+    assert np.array_equal(cr[how == 1], bl[how == 1])
+    assert np.all(bhow[how == 2] == 2) and np.all(np.isnan(cr[how == 2]))
+    assert not np.isnan(cr[how == 0]).any()
