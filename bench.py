@@ -105,7 +105,12 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
+
+    def mark(self, name):
+        """Host time of a point of the run; summary(start, stop) keeps the
+        samples read between two marks."""
+        setattr(self, "t_" + name, time.perf_counter())
 
     def __exit__(self, *a):
         if self.proc is not None:
@@ -116,10 +121,14 @@ class ClockSampler:
                 self.proc.kill()
             self.t.join(timeout=2)
 
-    def summary(self):
+    def summary(self, start=None, stop=None):
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        t0 = getattr(self, "t_" + start, None) if start else None
+        t1 = getattr(self, "t_" + stop, None) if stop else None
+        for t, ln in self.lines:
+            if (t0 is not None and t < t0) or (t1 is not None and t > t1 + 0.25):
+                continue
             p = [v.strip() for v in ln.split(",")]
             if len(p) < 9:
                 continue
@@ -414,28 +423,35 @@ def bench_ours(args):
             import torch.distributed as dist
             dist.barrier()
 
-    for _ in range(args.warmup):
-        step(False)
-    torch.cuda.synchronize()
-    barrier()
-    bg.profile_read(ctx)  # discard anything recorded so far
-    bg.profile_enable(ctx, True)
-    launches0 = bg.launch_count()
-    start = torch.cuda.Event(enable_timing=True)
-    stop = torch.cuda.Event(enable_timing=True)
+    # the clock sampler starts before the warm-up, so that the start of
+    # nvidia-smi falls outside the timed region; only the samples read while
+    # the timed steps ran are kept
     with ClockSampler(local) as clk:
+        for _ in range(args.warmup):
+            step(False)
         torch.cuda.synchronize()
+        barrier()
+        bg.profile_read(ctx)  # discard anything recorded so far
+        bg.profile_enable(ctx, True)
+        launches0 = bg.launch_count()
+        start = torch.cuda.Event(enable_timing=True)
+        stop = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        clk.mark("start")
         start.record(stream)
         for _ in range(args.steps):
             step(True)
         stop.record(stream)
         torch.cuda.synchronize()
+        clk.mark("stop")
     launches = bg.launch_count() - launches0
     prof = bg.profile_read(ctx)
     bg.profile_enable(ctx, False)
     barrier()
     ms = start.elapsed_time(stop) / args.steps
     stage = {k: statistics.median(a.elapsed_time(b) for a, b in v) for k, v in ev.items()}
+    per_step = [sum(a.elapsed_time(b) for a, b in (ev[k][i] for k in ev)) for i in range(args.steps)]
+    lead_ms = start.elapsed_time(ev["hash"][0][0])  # timed region before the first step ran
     if ws > 1:
         import torch.distributed as dist
         t = torch.tensor([ms], device=dev)
@@ -481,7 +497,7 @@ def bench_ours(args):
         solve_avg_ms = s_ms / max(s_launch, 1)
         nodes_per_launch = s_nodes / max(s_launch, 1)
         achieved = okrige_flops_per_node() * nodes_per_launch / (solve_avg_ms / 1e3) / 1e12
-        clocks = clk.summary()
+        clocks = clk.summary("start", "stop")
         out = {
             "metric": METRIC, "value": value, "unit": "nodes/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
@@ -490,6 +506,7 @@ def bench_ours(args):
             "stages_ms": {"hash_build": stage["hash"], "idw_k16": stage["idw"],
                           "kriging_k32": stage["ok"]},
             "kernels_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+            "step_ms": [round(t, 3) for t in per_step], "lead_ms": round(lead_ms, 3),
             "idw_nodes_per_s": m / (stage["idw"] / 1e3),
             "kriging_nodes_per_s": m / (stage["ok"] / 1e3),
             "roofline": {"bound": "alu", "kernel": "k_okrige_solve<32> (kriging k=32 solve)",

@@ -153,6 +153,24 @@ bg_status bg_interp_okrige(bg_soundings_t s, bg_grid_t grid, int k, const bg_var
                            float* depth_out, float* var_out, int32_t* nbr_out,
                            void* cuda_stream);
 
+/* The same two methods at a list of query points instead of grid nodes: the
+ * paper's hole filling interpolates the missing entries of a grid (Sec. IV,
+ * Grid B) and its runtime tests interpolate batches of generated points
+ * (Sec. IV, Grid A). Neighbours, weights and outputs follow the two calls
+ * above exactly; a grid's nodes passed as points give bitwise the grid's
+ * results.
+ *   qx_cm, qy_cm: device, m int32 each: query coordinates in cm; a point
+ *     outside (-2^30, 2^30) cm gets NaN outputs (and -1 neighbours). Points
+ *     in scan order (each near the previous one) run fastest.
+ *   m in [0, 2^40); outputs (device) have m entries (nbr_out m*k).
+ * Asynchronous on cuda_stream; the caller synchronizes. */
+bg_status bg_interp_idw_points(bg_soundings_t s, const int32_t* qx_cm, const int32_t* qy_cm,
+                               int64_t m, int k, float power, float* depth_out, int32_t* nbr_out,
+                               void* cuda_stream);
+bg_status bg_interp_okrige_points(bg_soundings_t s, const int32_t* qx_cm, const int32_t* qy_cm,
+                                  int64_t m, int k, const bg_variogram* v, float* depth_out,
+                                  float* var_out, int32_t* nbr_out, void* cuda_stream);
+
 /* ---------------------------------------------------------------- serving */
 
 /* A gridding request for bg_submit. Inputs and outputs are HOST memory; the

@@ -25,8 +25,10 @@ OKRIGE = 1
 
 __all__ = [
     "BGError", "Variogram", "SoundingsInfo", "SPHERICAL", "EXPONENTIAL", "IDW", "OKRIGE",
-    "version", "launch_count", "profile_enable", "profile_read", "ctx_create", "ctx_destroy", "ctx_device_bytes", "grid_create", "grid_destroy",
+    "version", "launch_count", "profile_enable", "profile_read", "ctx_create", "ctx_destroy",
+    "ctx_device_bytes", "grid_create", "grid_destroy",
     "soundings_upload", "soundings_info", "soundings_destroy", "interp_idw", "interp_okrige",
+    "interp_idw_points", "interp_okrige_points",
     "variogram", "interp_idw_noalloc", "submit", "poll", "wait", "cancel", "serve_stats",
     "serve_shutdown", "Request", "Result", "Batch", "batch_create", "batch_run", "batch_tune",
     "batch_set_cell_target", "batch_status", "batch_destroy",
@@ -176,6 +178,39 @@ def interp_okrige(s, grid, k: int, vgm: Variogram, depth_out, var_out=None, nbr_
         _check_dtype(nbr_out, "int32")
     check(_lib().bg_interp_okrige(s, grid, k, ctypes.byref(vgm), _ptr(depth_out), _ptr(var_out),
                                   _ptr(nbr_out), _stream(stream, depth_out)), "bg_interp_okrige")
+
+
+def _check_points(qx_cm, qy_cm, depth_out):
+    for t, dt in ((qx_cm, "int32"), (qy_cm, "int32"), (depth_out, "float32")):
+        _check_dtype(t, dt)
+    m = int(qx_cm.shape[0])
+    if int(qy_cm.shape[0]) != m or int(depth_out.shape[0]) < m:
+        raise ValueError("qx, qy and depth_out must hold m entries")
+    return m
+
+
+def interp_idw_points(s, qx_cm, qy_cm, k: int, power: float, depth_out, nbr_out=None,
+                      stream=None) -> None:
+    """IDW at query points (device int32 cm arrays) into depth_out (device, m float32)."""
+    m = _check_points(qx_cm, qy_cm, depth_out)
+    if nbr_out is not None:
+        _check_dtype(nbr_out, "int32")
+    check(_lib().bg_interp_idw_points(s, _ptr(qx_cm), _ptr(qy_cm), m, k, power, _ptr(depth_out),
+                                      _ptr(nbr_out), _stream(stream, depth_out)),
+          "bg_interp_idw_points")
+
+
+def interp_okrige_points(s, qx_cm, qy_cm, k: int, vgm: Variogram, depth_out, var_out=None,
+                         nbr_out=None, stream=None) -> None:
+    """Ordinary kriging at query points (device int32 cm arrays)."""
+    m = _check_points(qx_cm, qy_cm, depth_out)
+    if var_out is not None:
+        _check_dtype(var_out, "float32")
+    if nbr_out is not None:
+        _check_dtype(nbr_out, "int32")
+    check(_lib().bg_interp_okrige_points(s, _ptr(qx_cm), _ptr(qy_cm), m, k, ctypes.byref(vgm),
+                                         _ptr(depth_out), _ptr(var_out), _ptr(nbr_out),
+                                         _stream(stream, depth_out)), "bg_interp_okrige_points")
 
 
 def interp_idw_noalloc(x_cm, y_cm, z_m, grid_spec, k: int, power: float, depth_out,

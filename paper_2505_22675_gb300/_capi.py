@@ -87,6 +87,10 @@ _SIGNATURES = {
     "bg_interp_idw": ([P, P, ctypes.c_int, ctypes.c_float, P, P, P], ctypes.c_int),
     "bg_interp_okrige": ([P, P, ctypes.c_int, ctypes.POINTER(Variogram), P, P, P, P],
                          ctypes.c_int),
+    "bg_interp_idw_points": ([P, P, P, ctypes.c_int64, ctypes.c_int, ctypes.c_float, P, P, P],
+                             ctypes.c_int),
+    "bg_interp_okrige_points": ([P, P, P, ctypes.c_int64, ctypes.c_int, ctypes.POINTER(Variogram),
+                                 P, P, P, P], ctypes.c_int),
     "bg_submit": ([P, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
     "bg_poll": ([P, ctypes.c_uint64, ctypes.POINTER(Result)], ctypes.c_int),
     "bg_wait": ([P, ctypes.c_uint64, ctypes.c_int, ctypes.POINTER(Result)], ctypes.c_int),

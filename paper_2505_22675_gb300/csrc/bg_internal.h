@@ -50,6 +50,13 @@ struct GridView {
     int32_t x0, y0, cell, nx, ny;
 };
 
+// Query points: m device coordinates (cm) in two arrays.
+struct PointsView {
+    const int32_t* x;
+    const int32_t* y;
+    int64_t m;
+};
+
 struct OkParams {
     int32_t model;
     float c0;      // nugget
@@ -185,5 +192,12 @@ bg_status launch_idw(const bg_soundings_s* s, const GridView& g, int k, float po
                      float* depth, int32_t* nbr, cudaStream_t st);
 bg_status launch_okrige(const bg_soundings_s* s, const GridView& g, int k, const OkParams& p,
                         float* depth, float* var, int32_t* nbr, cudaStream_t st);
+
+// The same at a list of query points.
+bg_status launch_idw_points(const bg_soundings_s* s, const PointsView& q, int k, float power,
+                            float* depth, int32_t* nbr, cudaStream_t st);
+bg_status launch_okrige_points(const bg_soundings_s* s, const PointsView& q, int k,
+                               const OkParams& p, float* depth, float* var, int32_t* nbr,
+                               cudaStream_t st);
 
 }  // namespace bg

@@ -76,7 +76,93 @@ bg_status launch_k(const HashView& h, const GridView& g, int k, float power, flo
     return BG_OK;
 }
 
+// Query points: kStrip consecutive points per thread (knn_chain).
+template <int K>
+__global__ void __launch_bounds__(128) k_idw_pts(HashView h, PointsView q, int k, float power,
+                                                 float* __restrict__ depth,
+                                                 int32_t* __restrict__ nbr, int* __restrict__ flag) {
+    __shared__ uint64_t heap[K * 128];
+    const int64_t p0 = ((int64_t)blockIdx.x * 128 + threadIdx.x) * kStrip;
+    if (p0 >= q.m) return;
+    uint64_t* hp = heap + threadIdx.x;
+    const int bits = h.idx_bits;
+    const uint64_t mask = (1ull << bits) - 1;
+    auto none = [&](int64_t p) {
+        depth[p] = __int_as_float(0x7fc00000);
+        if (nbr)
+            for (int i = 0; i < k; ++i) nbr[p * k + i] = -1;
+    };
+    if (h.n_valid == 0) {
+        for (int64_t p = p0; p < min(p0 + kStrip, q.m); ++p) none(p);
+        return;
+    }
+    knn_chain<128>(h, q.x, q.y, p0, q.m, K, hp, flag, [&](int64_t p, int cnt) {
+        if (cnt < 0) {
+            none(p);
+            return;
+        }
+        const int keff = min(cnt, k);
+        depth[p] = idw_from(h, keff, power, [&](int i, uint64_t& dd, int& ii) {
+            const uint64_t key = hp[i * 128];
+            dd = key >> bits;
+            ii = (int)(key & mask);
+        });
+        if (nbr) {
+            int32_t* out = nbr + p * k;
+            for (int i = 0; i < k; ++i) out[i] = i < keff ? (int)(hp[i * 128] & mask) : -1;
+        }
+    });
+}
+
+template <int K>
+__global__ void __launch_bounds__(128) k_idw_pts_wide(HashView h, PointsView q, int k, float power,
+                                                      float* __restrict__ depth,
+                                                      int32_t* __restrict__ nbr,
+                                                      int* __restrict__ flag) {
+    if (*(volatile int*)flag == 0) return;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < q.m;
+         p += (int64_t)gridDim.x * blockDim.x)
+        idw_point_wide<K>(h, __ldg(q.x + p), __ldg(q.y + p), k, power, depth + p,
+                          nbr ? nbr + p * k : nullptr);
+}
+
+template <int K>
+bg_status launch_pts_k(const HashView& h, const PointsView& q, int k, float power, float* depth,
+                       int32_t* nbr, int* d_flag, cudaStream_t st, bg_ctx_s* prof_ctx) {
+    const int64_t threads = (q.m + kStrip - 1) / kStrip;
+    const int64_t nb = (threads + 127) / 128;
+    BG_CUDA(cudaMemsetAsync(d_flag, 0, sizeof(int), st));
+    {
+        ProfScope ps(prof_ctx, kProfIdw, q.m, st);
+        k_idw_pts<K><<<(unsigned)nb, 128, 0, st>>>(h, q, k, power, depth, nbr, d_flag);
+    }
+    k_idw_pts_wide<K><<<(unsigned)std::min<int64_t>((q.m + 127) / 128, 152 * 4), 128, 0, st>>>(
+        h, q, k, power, depth, nbr, d_flag);
+    note_launches(2);
+    BG_CUDA(cudaGetLastError());
+    return BG_OK;
+}
+
 }  // namespace
+
+bg_status launch_idw_points(const bg_soundings_s* s, const PointsView& q, int k, float power,
+                            float* depth, int32_t* nbr, cudaStream_t st) {
+    if (q.m == 0) return BG_OK;
+    HashView h = s->h;
+    const int K = k <= 4 ? 4 : k <= 8 ? 8 : k <= 16 ? 16 : 32;
+    h.r0 = start_halfwidth(s, K);
+    int* flag = nullptr;
+    bg_status rc = dalloc(s->ctx, (void**)&flag, sizeof(int), st);
+    if (rc != BG_OK) return rc;
+    switch (K) {
+        case 4: rc = launch_pts_k<4>(h, q, k, power, depth, nbr, flag, st, s->ctx); break;
+        case 8: rc = launch_pts_k<8>(h, q, k, power, depth, nbr, flag, st, s->ctx); break;
+        case 16: rc = launch_pts_k<16>(h, q, k, power, depth, nbr, flag, st, s->ctx); break;
+        default: rc = launch_pts_k<32>(h, q, k, power, depth, nbr, flag, st, s->ctx); break;
+    }
+    dfree(s->ctx, flag, sizeof(int), st);
+    return rc;
+}
 
 bg_status launch_idw(const bg_soundings_s* s, const GridView& g, int k, float power,
                      float* depth, int32_t* nbr, cudaStream_t st) {

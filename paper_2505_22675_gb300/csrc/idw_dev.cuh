@@ -102,4 +102,24 @@ __device__ __forceinline__ void idw_node(const HashView& h, const GridView& g, i
     }
 }
 
+// Wide-key IDW of one query point whose table bound does not fit the packed
+// key (the rare pass after knn_chain flagged a point); other points return.
+template <int K>
+__device__ __forceinline__ void idw_point_wide(const HashView& h, int qx, int qy, int k,
+                                               float power, float* __restrict__ dout,
+                                               int32_t* __restrict__ o) {
+    if (h.n_valid == 0 || !query_in_range(qx, qy)) return;
+    const Bound b = knn_bound<K>(h, qx, qy);
+    if (packed_fits(h, b.tau0)) return;
+    uint64_t d2[K];
+    int id[K];
+    const int keff = min(knn_scan<K, true>(h, qx, qy, b, d2, id), k);
+    *dout = idw_from(h, keff, power, [&](int i, uint64_t& dd, int& ii) {
+        dd = d2[i];
+        ii = id[i];
+    });
+    if (o)
+        for (int i = 0; i < k; ++i) o[i] = i < keff ? id[i] : -1;
+}
+
 }  // namespace bg

@@ -394,4 +394,64 @@ __device__ __forceinline__ void knn_strip(const HashView& h, const GridView& g, 
     }
 }
 
+// ---------------------------------------------------------------------------
+// Query points instead of grid nodes. A thread takes kStrip consecutive points
+// of the caller's list. The next point's K-th distance is at most the previous
+// point's plus the distance between the two (triangle inequality); that bound
+// is used when the step is no longer than the previous K-th distance (lists
+// in scan order, such as the holes of a grid), else the summed-area table's.
+
+constexpr int32_t kQueryLimit = 1 << 30;  // query coordinates lie in (-2^30, 2^30) cm
+
+__device__ __forceinline__ bool query_in_range(int qx, int qy) {
+    return qx > -kQueryLimit && qx < kQueryLimit && qy > -kQueryLimit && qy < kQueryLimit;
+}
+
+// Packed-key k-NN of points p0 .. p0 + kStrip - 1 (those below m). emit(p, cnt)
+// runs after each point with its keys sorted ascending in hp[0 .. cnt), or
+// with cnt = -1 for a point outside the coordinate range; a point whose table
+// bound does not fit the packed key is left to the wide pass (*flag = 1).
+template <int S, class Emit>
+__device__ __forceinline__ void knn_chain(const HashView& h, const int32_t* __restrict__ px,
+                                          const int32_t* __restrict__ py, int64_t p0, int64_t m,
+                                          int kc, uint64_t* hp, int* flag, Emit emit) {
+    int64_t prev = -1;  // K-th squared distance of the previous point, -1 if none
+    int qxp = 0, qyp = 0;
+    for (int s = 0; s < kStrip; ++s) {
+        const int64_t p = p0 + s;
+        if (p >= m) break;
+        const int qx = __ldg(px + p), qy = __ldg(py + p);
+        if (!query_in_range(qx, qy)) {
+            emit(p, -1);
+            prev = -1;
+            continue;
+        }
+        Bound b{0, 0};
+        bool ok = false;
+        if (prev >= 0 && prev < ((int64_t)1 << 60)) {  // r below 2^31 + 4: r * r cannot wrap
+            const int64_t dx = (int64_t)qx - qxp, dy = (int64_t)qy - qyp;
+            const int64_t step2 = dx * dx + dy * dy;
+            if (step2 <= prev) {
+                const int64_t r = isqrt_ub(prev) + isqrt_ub(step2);  // >= d_K(prev) + |step|
+                b.tau0 = r * r;
+                b.cy = clamp_cell(h, (int64_t)qy - h.hy0, h.ncy);
+                ok = packed_fits(h, b.tau0);
+            }
+        }
+        if (!ok) {
+            b = knn_bound_rt(h, qx, qy, kc);
+            if (!packed_fits(h, b.tau0)) {
+                *flag = 1;
+                prev = -1;
+                continue;
+            }
+        }
+        const int cnt = knn_scan_heap_rt<S>(h, qx, qy, b, hp, kc);
+        prev = cnt == kc ? (int64_t)(hp[(kc - 1) * S] >> h.idx_bits) : -1;
+        qxp = qx;
+        qyp = qy;
+        emit(p, cnt);
+    }
+}
+
 }  // namespace bg

@@ -104,7 +104,113 @@ bg_status launch_k(const HashView& h, const GridView& g, int k, const OkParams& 
     return rc;
 }
 
+// ------------------------------------------------------------ query points
+
+// points [p0, p1), kStrip consecutive points per thread
+template <int K>
+__global__ void __launch_bounds__(128) k_knn_ids_pts(HashView h, PointsView q, int k, int64_t p0,
+                                                     int64_t p1, int32_t* __restrict__ ids,
+                                                     int* __restrict__ flag) {
+    __shared__ uint64_t heap[K * 128];
+    const int64_t a = p0 + ((int64_t)blockIdx.x * 128 + threadIdx.x) * kStrip;
+    if (a >= p1) return;
+    uint64_t* hp = heap + threadIdx.x;
+    if (h.n_valid == 0) {
+        for (int64_t p = a; p < min(a + kStrip, p1); ++p)
+            for (int i = 0; i < k; ++i) ids[(p - p0) * k + i] = -1;
+        return;
+    }
+    const uint64_t mask = (1ull << h.idx_bits) - 1;
+    knn_chain<128>(h, q.x, q.y, a, p1, K, hp, flag, [&](int64_t p, int cnt) {
+        int32_t* out = ids + (p - p0) * k;
+        for (int i = 0; i < k; ++i) out[i] = i < cnt ? (int)(hp[i * 128] & mask) : -1;
+    });
+}
+
+template <int K>
+__global__ void __launch_bounds__(128) k_knn_ids_pts_wide(HashView h, PointsView q, int k,
+                                                          int64_t p0, int64_t p1,
+                                                          int32_t* __restrict__ ids,
+                                                          int* __restrict__ flag) {
+    if (*(volatile int*)flag == 0) return;
+    for (int64_t p = p0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < p1;
+         p += (int64_t)gridDim.x * blockDim.x)
+        knn_ids_point_wide<K>(h, __ldg(q.x + p), __ldg(q.y + p), k, ids + (p - p0) * k);
+}
+
+template <int K>
+__global__ void __launch_bounds__(kSolveWarps * 32) k_okrige_solve_pts(
+    HashView h, PointsView q, int k, OkParams p, int64_t p0, int64_t nodes,
+    const int32_t* __restrict__ ids, float* __restrict__ depth, float* __restrict__ var) {
+    __shared__ float smem[kSolveWarps * Geo<K>::WARP_FLOATS];
+    okrige_solve_block<K, true>(h, GridView{}, k, p, p0, nodes, ids, depth, var, blockIdx.x, smem,
+                                q.x, q.y);
+}
+
+template <int K>
+bg_status launch_pts_k(const HashView& h, const PointsView& q, int k, const OkParams& p,
+                       float* depth, float* var, int32_t* nbr, bg_ctx_s* ctx, cudaStream_t st) {
+    using Gm = Geo<K>;
+    // points per chunk: the id buffer stays near 1 GiB unless the caller
+    // passed nbr_out, which then holds all ids
+    int64_t per = q.m;
+    if (!nbr) per = std::min<int64_t>(q.m, std::max<int64_t>(4096, ((int64_t)1 << 28) / k));
+    const size_t flag_bytes = 256;
+    const size_t id_bytes = nbr ? 0 : (size_t)per * k * sizeof(int32_t);
+    void* scratch = nullptr;
+    bg_status rc = dalloc(ctx, &scratch, flag_bytes + id_bytes, st);
+    if (rc != BG_OK) return rc;
+    int* flag = (int*)scratch;
+    const int64_t sys_per_block = (int64_t)kSolveWarps * Gm::SYS * kRounds;
+    for (int64_t p0 = 0; p0 < q.m; p0 += per) {
+        const int64_t p1 = std::min<int64_t>(q.m, p0 + per);
+        const int64_t n = p1 - p0;
+        int32_t* chunk_ids = nbr ? nbr + p0 * k : (int32_t*)((char*)scratch + flag_bytes);
+        cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), st);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "memset");
+            break;
+        }
+        const int64_t nb = ((n + kStrip - 1) / kStrip + 127) / 128;
+        {
+            ProfScope ps(ctx, kProfKnnIds, n, st);
+            k_knn_ids_pts<K><<<(unsigned)nb, 128, 0, st>>>(h, q, k, p0, p1, chunk_ids, flag);
+        }
+        k_knn_ids_pts_wide<K><<<(unsigned)std::min<int64_t>((n + 127) / 128, 152 * 4), 128, 0, st>>>(
+            h, q, k, p0, p1, chunk_ids, flag);
+        const int64_t sb = (n + sys_per_block - 1) / sys_per_block;
+        {
+            ProfScope ps(ctx, kProfSolve, n, st);
+            k_okrige_solve_pts<K><<<(unsigned)sb, kSolveWarps * 32, 0, st>>>(h, q, k, p, p0, n,
+                                                                             chunk_ids, depth, var);
+        }
+        note_launches(3);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "kriging launch");
+            break;
+        }
+    }
+    dfree(ctx, scratch, flag_bytes + id_bytes, st);
+    return rc;
+}
+
 }  // namespace
+
+bg_status launch_okrige_points(const bg_soundings_s* s, const PointsView& q, int k,
+                               const OkParams& p, float* depth, float* var, int32_t* nbr,
+                               cudaStream_t st) {
+    if (q.m == 0) return BG_OK;
+    HashView h = s->h;
+    const int K = k <= 4 ? 4 : k <= 8 ? 8 : k <= 16 ? 16 : 32;
+    h.r0 = start_halfwidth(s, K);
+    switch (K) {
+        case 4: return launch_pts_k<4>(h, q, k, p, depth, var, nbr, s->ctx, st);
+        case 8: return launch_pts_k<8>(h, q, k, p, depth, var, nbr, s->ctx, st);
+        case 16: return launch_pts_k<16>(h, q, k, p, depth, var, nbr, s->ctx, st);
+        default: return launch_pts_k<32>(h, q, k, p, depth, var, nbr, s->ctx, st);
+    }
+}
 
 bg_status launch_okrige(const bg_soundings_s* s, const GridView& g, int k, const OkParams& p,
                         float* depth, float* var, int32_t* nbr, cudaStream_t st) {

@@ -128,6 +128,22 @@ __device__ __forceinline__ void knn_ids_node(const HashView& h, const GridView& 
     }
 }
 
+// Wide-key neighbour ids of one query point whose table bound does not fit
+// the packed key; other points return.
+template <int K>
+__device__ __forceinline__ void knn_ids_point_wide(const HashView& h, int qx, int qy, int k,
+                                                   int32_t* __restrict__ o) {
+    if (h.n_valid == 0 || !query_in_range(qx, qy)) return;
+    const Bound b = knn_bound<K>(h, qx, qy);
+    if (packed_fits(h, b.tau0)) return;
+    uint64_t d2[K];
+    int id[K];
+    const int keff = knn_scan<K, true>(h, qx, qy, b, d2, id);
+#pragma unroll
+    for (int i = 0; i < K; ++i)
+        if (i < k) o[i] = i < keff ? id[i] : -1;
+}
+
 // ---------------------------------------------------------------- solve
 
 __host__ __device__ constexpr int tri(int r) { return r * (r + 1) / 2; }
@@ -219,13 +235,17 @@ __device__ __forceinline__ int exp_above(float v) { return ((__float_as_int(v) >
 // The kriging systems of solve block `blk` (kSolveWarps warps x SYS systems x
 // kRounds rounds) of a range of `nodes` grid nodes starting at node0, with the
 // neighbour ids of node node0 + i at ids[i * k]. smem: kSolveWarps * WARP_FLOATS.
-template <int K>
+// With kPts the "nodes" are query points whose coordinates are px[], py[]
+// (g unused).
+template <int K, bool kPts = false>
 __device__ __forceinline__ void okrige_solve_block(const HashView& h, const GridView& g, int k,
                                                    const OkParams& p, int64_t node0, int64_t nodes,
                                                    const int32_t* __restrict__ ids,
                                                    float* __restrict__ depth,
                                                    float* __restrict__ var, int64_t blk,
-                                                   float* smem) {
+                                                   float* smem,
+                                                   const int32_t* __restrict__ px = nullptr,
+                                                   const int32_t* __restrict__ py = nullptr) {
     using Gm = Geo<K>;
     constexpr int G = Gm::G;
     constexpr int ROW = Gm::ROW;
@@ -258,8 +278,14 @@ __device__ __forceinline__ void okrige_solve_block(const HashView& h, const Grid
         }
         const int id0 = live ? __ldg(my) : -1;
         const int ke = (id0 >= 0) ? 1 + (int)cnt : 0;  // 0: no output (no data, or past the end)
-        const int qx = g.x0 + (int)(node % g.nx) * g.cell + g.cell / 2;
-        const int qy = g.y0 + (int)(node / g.nx) * g.cell + g.cell / 2;
+        int qx, qy;
+        if constexpr (kPts) {
+            qx = __ldg(px + node);
+            qy = __ldg(py + node);
+        } else {
+            qx = g.x0 + (int)(node % g.nx) * g.cell + g.cell / 2;
+            qy = g.y0 + (int)(node / g.nx) * g.cell + g.cell / 2;
+        }
 
         // gather the neighbours' records; offsets from neighbour 0 as exact floats
         int4 r0 = make_int4(0, 0, 0, 0);

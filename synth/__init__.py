@@ -24,8 +24,8 @@ import math
 import numpy as np
 
 __all__ = [
-    "GridSpec", "Workload", "bumps", "seafloor", "to_cm", "tile", "swath",
-    "batched_tiles",
+    "GridSpec", "Workload", "HoleGrid", "bumps", "seafloor", "to_cm", "tile", "swath",
+    "batched_tiles", "hole_grid", "row_midpoints", "random_points",
 ]
 
 BUMP_DENSITY_PER_M2 = 40.0 / (512.0 * 512.0)
@@ -229,3 +229,126 @@ def batched_tiles(seed: int = 3, count: int = 512, median_n: int = 20_000, sigma
         w.name = f"batch{t}"
         out.append((w, method))
     return out
+
+
+# ------------------------------------------------------- gridded workloads
+
+@dataclasses.dataclass
+class HoleGrid:
+    """A regular depth grid with a random fraction of its nodes removed.
+
+    grid: the node lattice; z_full: float32 [ny * nx] true depths, row-major;
+    holes: sorted int64 indices of the removed nodes.
+    """
+    grid: GridSpec
+    z_full: np.ndarray
+    holes: np.ndarray
+    frac: float
+    seed: int
+
+    def node_xy(self, idx: np.ndarray):
+        g = self.grid
+        i = idx % g.nx
+        j = idx // g.nx
+        return ((g.x0_cm + i * g.cell_cm + g.cell_cm // 2).astype(np.int32),
+                (g.y0_cm + j * g.cell_cm + g.cell_cm // 2).astype(np.int32))
+
+    def kept(self) -> np.ndarray:
+        mask = np.ones(self.grid.m, dtype=bool)
+        mask[self.holes] = False
+        return np.flatnonzero(mask)
+
+    def soundings(self) -> Workload:
+        """The kept nodes as soundings (row-major order)."""
+        idx = self.kept()
+        x, y = self.node_xy(idx)
+        return Workload(x, y, self.z_full[idx].copy(), self.grid, f"holes{self.frac}",
+                        dict(seed=self.seed, frac=self.frac))
+
+    def queries(self):
+        """(qx_cm, qy_cm) of the removed nodes, in row-major order."""
+        return self.node_xy(self.holes)
+
+    def truth(self) -> np.ndarray:
+        return self.z_full[self.holes]
+
+    def source(self) -> np.ndarray:
+        """The grid as float32 [ny * nx] with NaN at the removed nodes."""
+        z = self.z_full.copy()
+        z[self.holes] = np.nan
+        return z
+
+
+def _lattice_field(x_m: np.ndarray, y_m: np.ndarray, table: np.ndarray, cut_sigmas=5.0):
+    """Bump field on the lattice x_m (columns) by y_m (rows), both ascending and
+    evenly spaced: each Gaussian is separable, so it is added as an outer
+    product over the window of nodes within cut_sigmas of its centre."""
+    field = np.zeros((y_m.size, x_m.size), dtype=np.float64)
+    dx = x_m[1] - x_m[0] if x_m.size > 1 else 1.0
+    dy = y_m[1] - y_m[0] if y_m.size > 1 else 1.0
+    for cx, cy, a, s in table:
+        rad = cut_sigmas * s
+        i0 = max(0, int(math.floor((cx - rad - x_m[0]) / dx)))
+        i1 = min(x_m.size, int(math.ceil((cx + rad - x_m[0]) / dx)) + 1)
+        j0 = max(0, int(math.floor((cy - rad - y_m[0]) / dy)))
+        j1 = min(y_m.size, int(math.ceil((cy + rad - y_m[0]) / dy)) + 1)
+        if i0 >= i1 or j0 >= j1:
+            continue
+        ex = np.exp(-((x_m[i0:i1] - cx) ** 2) / (2 * s * s))
+        ey = np.exp(-((y_m[j0:j1] - cy) ** 2) / (2 * s * s))
+        field[j0:j1, i0:i1] += a * np.outer(ey, ex)
+    return field
+
+
+def hole_grid(seed: int = 4, nx: int = 4096, ny: int = 4096, cell_cm: int = 200,
+              frac: float = 0.05, x0_cm: int = 0, y0_cm: int = 0,
+              noise_m: float = 0.0) -> HoleGrid:
+    """A gridded bathymetry product with round(frac * nx * ny) nodes removed at
+    random (the shape of the paper's hole-filling tests, Sec. IV Grid B).
+
+    The depth of node (i, j) is the shared seafloor model at its centre (bumps
+    cut at 5 sigma), plus N(0, noise_m^2) if noise_m > 0. The removed nodes are
+    drawn without replacement from the same seeded generator.
+    """
+    if not 0.0 <= frac < 1.0:
+        raise ValueError("frac must be in [0, 1)")
+    rng = _rng(seed)
+    xs = (x0_cm + np.arange(nx) * cell_cm + cell_cm // 2) / 100.0
+    ys = (y0_cm + np.arange(ny) * cell_cm + cell_cm // 2) / 100.0
+    table = bumps(rng, x0_cm / 100.0, (x0_cm + nx * cell_cm) / 100.0,
+                  y0_cm / 100.0, (y0_cm + ny * cell_cm) / 100.0)
+    field = _lattice_field(xs, ys, table)
+    z = 3500.0 + 0.01 * xs[None, :] + field
+    if noise_m > 0:
+        z = z + rng.normal(0.0, noise_m, z.shape)
+    m = nx * ny
+    holes = np.sort(rng.choice(m, size=int(round(frac * m)), replace=False)).astype(np.int64)
+    return HoleGrid(GridSpec(x0_cm, y0_cm, cell_cm, nx, ny), z.astype(np.float32).ravel(),
+                    holes, frac, seed)
+
+
+def row_midpoints(grid: GridSpec):
+    """Query points halfway between successive grid rows, on every node column:
+    the shape of the paper's row-filling tests (Sec. IV Grid A, latitudes added
+    between existing ones). Returns (qx_cm, qy_cm), (ny - 1) * nx points, row-major.
+    """
+    i = np.arange(grid.nx)
+    j = np.arange(grid.ny - 1)
+    qx = grid.x0_cm + i * grid.cell_cm + grid.cell_cm // 2
+    qy = grid.y0_cm + (j + 1) * grid.cell_cm
+    X, Y = np.meshgrid(qx, qy)
+    return X.ravel().astype(np.int32), Y.ravel().astype(np.int32)
+
+
+def random_points(seed: int, grid: GridSpec, m: int, margin_cells: float = 0.0):
+    """m uniform query points (int32 cm) over the grid's node hull, widened by
+    margin_cells on every side."""
+    rng = _rng(seed)
+    c = grid.cell_cm
+    lo_x = grid.x0_cm + c // 2 - margin_cells * c
+    hi_x = grid.x0_cm + (grid.nx - 1) * c + c // 2 + margin_cells * c
+    lo_y = grid.y0_cm + c // 2 - margin_cells * c
+    hi_y = grid.y0_cm + (grid.ny - 1) * c + c // 2 + margin_cells * c
+    qx = np.floor(rng.uniform(lo_x, hi_x + 1, m)).astype(np.int32)
+    qy = np.floor(rng.uniform(lo_y, hi_y + 1, m)).astype(np.int32)
+    return qx, qy

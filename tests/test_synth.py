@@ -36,3 +36,32 @@ def test_full_swath_geometry_constants():
 def test_batched_tiles_mix():
     tiles = synth.batched_tiles(seed=3, count=6, scale=0.01)
     assert len(tiles) == 6 and all(m in (0, 1) for _, m in tiles)
+
+
+def test_hole_grid_partitions_the_nodes():
+    h = synth.hole_grid(seed=31, nx=50, ny=40, cell_cm=200, frac=0.07)
+    h2 = synth.hole_grid(seed=31, nx=50, ny=40, cell_cm=200, frac=0.07)
+    assert np.array_equal(h.z_full, h2.z_full) and np.array_equal(h.holes, h2.holes)
+    assert h.holes.size == round(0.07 * 2000)
+    assert np.all(np.diff(h.holes) > 0)
+    kept = h.kept()
+    assert kept.size + h.holes.size == 2000 and np.intersect1d(kept, h.holes).size == 0
+    s = h.soundings()
+    qx, qy = h.queries()
+    # node centres of a 2 m lattice: odd metres in cm
+    assert np.all((s.x_cm - 100) % 200 == 0) and np.all((qy - 100) % 200 == 0)
+    assert np.array_equal(s.z_m, h.z_full[kept]) and np.array_equal(h.truth(), h.z_full[h.holes])
+    src = h.source()
+    assert np.isnan(src[h.holes]).all() and not np.isnan(src[kept]).any()
+    assert 3300 < h.z_full.min() and h.z_full.max() < 3700
+
+
+def test_row_midpoints_and_random_points():
+    g = synth.GridSpec(1000, 2000, 200, 4, 3)
+    qx, qy = synth.row_midpoints(g)
+    assert qx.size == 4 * 2
+    assert set(np.unique(qy)) == {2200, 2400}
+    assert set(np.unique(qx)) == {1100, 1300, 1500, 1700}
+    rx, ry = synth.random_points(5, g, 1000, margin_cells=1)
+    assert rx.min() >= 1100 - 200 and rx.max() <= 1700 + 200
+    assert ry.min() >= 2100 - 200 and ry.max() <= 2500 + 200
