@@ -316,6 +316,98 @@ def batched_measure(bg, torch, ctx, pool, n_tiles, steps):
             "cell_target_tuned": best, "status_flags": status}
 
 
+def gridded_measure(bg, torch, n_side, fracs, steps=5):
+    """The paper's gridded-input tests on one synthetic depth grid of
+    n_side x n_side nodes at 2 m:
+    - row filling (Sec. IV Grid A): bilinear and Catmull-Rom onto the points
+      halfway between successive rows, with 5% of the source nodes missing;
+      HBM roofline over the algorithmic bytes (source read once, output written);
+    - hole filling (Sec. IV Grid B): for each removal fraction, the kept
+      nodes as soundings (hash build) and IDW k=16 + kriging k=32 at the
+      removed nodes; MAE / RMSE against the true depths.
+    Inputs and outputs are device-resident; both exceed L2."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    peaks = load_peaks()
+    hbm = peaks.get("hbm_gbs") or 6780.7
+    base = synth.hole_grid(seed=4, nx=n_side, ny=n_side, cell_cm=200, frac=0.05)
+    g = base.grid
+    spec = (g.x0_cm, g.y0_cm, g.cell_cm, g.nx, g.ny)
+    out = {"workload": f"synthetic depth grid {n_side} x {n_side} at 2 m (seafloor model, no "
+                       "noise); row filling onto the (n-1) x n row midpoints with 5% of the nodes "
+                       "missing; hole filling at removal fractions " + ", ".join(map(str, fracs)),
+           "resample": {}, "hole_filling": []}
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    src = torch.from_numpy(base.source()).to(dev)
+    mid = (g.x0_cm, g.y0_cm + g.cell_cm // 2, g.cell_cm, g.nx, g.ny - 1)
+    mo = mid[3] * mid[4]
+    res = torch.empty(mo, device=dev)
+    how = torch.empty(mo, dtype=torch.int8, device=dev)
+    for name, method in (("bilinear", bg.BILINEAR), ("catmull_rom", bg.CATMULL_ROM)):
+        ms = timed(lambda: bg.resample_grid(src, spec, method, mid, res, how))
+        nbytes = 4 * g.m + 4 * mo + mo  # source once, values, how-codes
+        counts = torch.bincount(how.long(), minlength=3).cpu().tolist()
+        out["resample"][name] = {
+            "ms": ms, "nodes_per_s": mo / (ms / 1e3),
+            "roofline": {"bound": "hbm", "achieved": nbytes / (ms / 1e3) / 1e9, "peak": hbm,
+                         "unit": "GB/s", "frac": nbytes / (ms / 1e3) / 1e9 / hbm,
+                         "bytes_per_node": nbytes / mo},
+            "by_method": counts[0], "bilinear_fallback": counts[1], "no_value": counts[2]}
+    del src, res, how
+
+    vgm = bg.variogram(*VGM)
+    ctx = bg.ctx_create(torch.cuda.current_device())
+    try:
+        for i, frac in enumerate(fracs):
+            hg = base.with_frac(frac, seed=100 + i)
+            sw = hg.soundings()
+            qx, qy = hg.queries()
+            truth = hg.truth().astype(np.float64)
+            xd, yd, zd = (torch.from_numpy(a).to(dev) for a in (sw.x_cm, sw.y_cm, sw.z_m))
+            qxd, qyd = torch.from_numpy(qx).to(dev), torch.from_numpy(qy).to(dev)
+            m = qx.size
+            di = torch.empty(m, device=dev)
+            do = torch.empty(m, device=dev)
+            vo = torch.empty(m, device=dev)
+            holder = {}
+
+            def build():
+                if "s" in holder:
+                    bg.soundings_destroy(holder.pop("s"))
+                holder["s"] = bg.soundings_upload(ctx, xd, yd, zd)
+
+            t_hash = timed(build)
+            s = holder["s"]
+            t_idw = timed(lambda: bg.interp_idw_points(s, qxd, qyd, IDW_K, IDW_P, di))
+            t_ok = timed(lambda: bg.interp_okrige_points(s, qxd, qyd, OK_K, vgm, do, vo))
+            bg.soundings_destroy(holder.pop("s"))
+
+            def err(d):
+                e = d.cpu().numpy().astype(np.float64) - truth
+                return {"mae_m": float(np.mean(np.abs(e))), "rmse_m": float(np.sqrt(np.mean(e * e))),
+                        "max_m": float(np.max(np.abs(e)))}
+            out["hole_filling"].append({
+                "frac": frac, "soundings": int(sw.x_cm.size), "holes": int(m),
+                "hash_build_ms": t_hash, "idw_ms": t_idw, "kriging_ms": t_ok,
+                "idw_points_per_s": m / (t_idw / 1e3), "kriging_points_per_s": m / (t_ok / 1e3),
+                "idw": err(di), "kriging": err(do)})
+            del xd, yd, zd, qxd, qyd, di, do, vo
+    finally:
+        bg.ctx_destroy(ctx)
+    return out
+
+
 def workload(args):
     if args.small:
         return synth.swath(seed=2, lines=2, pings=2000, beams=256)
@@ -550,6 +642,9 @@ def bench_ours(args):
                         serving_measure(bg, torch, sctx, pool, r, n_t, seed=17 + i))
             finally:
                 bg.ctx_destroy(sctx)
+        if not args.no_gridded:
+            out["gridded"] = gridded_measure(bg, torch, 4096 if args.small else 8192,
+                                             (0.01, 0.05, 0.1))
         if not args.no_cpu_baseline and ws == 1:
             out["cpu_baseline"] = cpu_baseline(w, target_s=args.cpu_seconds)
         print(json.dumps(out), flush=True)
@@ -576,10 +671,20 @@ def main():
     ap.add_argument("--serving-pool", type=int, default=48)
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-gridded", action="store_true",
+                    help="skip the gridded-input (row filling / hole filling) measurements")
+    ap.add_argument("--gridded-only", action="store_true",
+                    help="only the gridded-input measurements (one JSON line of their own)")
     ap.add_argument("--batch-tiles", type=int, default=512)
     args = ap.parse_args()
     if args.impl == "reference":
         bench_reference(args)
+    elif args.gridded_only:
+        import torch
+
+        import paper_2505_22675_gb300 as bg
+        print(json.dumps({"gridded": gridded_measure(bg, torch, 4096 if args.small else 8192,
+                                                     (0.01, 0.05, 0.1))}), flush=True)
     else:
         bench_ours(args)
 

@@ -171,6 +171,45 @@ bg_status bg_interp_okrige_points(bg_soundings_t s, const int32_t* qx_cm, const 
                                   int64_t m, int k, const bg_variogram* v, float* depth_out,
                                   float* var_out, int32_t* nbr_out, void* cuda_stream);
 
+/* ----------------------------------------------------------- gridded input */
+
+/* Resampling of a regular grid (the paper's stencil methods on gridded data):
+ *   BG_RESAMPLE_BILINEAR: the four nodes of the lattice cell that holds the
+ *     query, weighted as in Sec. III-A;
+ *   BG_RESAMPLE_CATMULL_ROM: the 4 x 4 nodes around that cell, the cubic C(t)
+ *     of Sec. III-B along x on each row, then along y; stencil indices past
+ *     the grid edge repeat the edge node.
+ * A node is needed when its weight is not zero (a query on a node line
+ * needs only that line). A needed NaN node (a missing value) gives NaN for
+ * bilinear, which has no fallback (Sec. III-D), and makes Catmull-Rom fall
+ * back to bilinear (Sec. III-B). A query outside the hull of the node
+ * centres gets NaN. Arithmetic is FP32 on anomalies from one needed node.
+ * No device memory is allocated; the calls are asynchronous on cuda_stream. */
+typedef enum bg_resample_method {
+    BG_RESAMPLE_BILINEAR = 0,
+    BG_RESAMPLE_CATMULL_ROM = 1
+} bg_resample_method;
+
+/* src: device, nx*ny float32 node values, row-major, node (i, j) at
+ *   (x0 + i*cell + cell/2, y0 + j*cell + cell/2) cm; cell even, nx, ny >= 2,
+ *   nodes inside (-2^30, 2^30) cm.
+ * qx_cm, qy_cm: device, m query coordinates (cm); out: device, m float32.
+ * how_out: NULL or device m int8: 0 the method's value, 1 the bilinear
+ *   fallback, 2 no value (NaN). */
+bg_status bg_resample_points(const float* src, int32_t x0_cm, int32_t y0_cm, int32_t cell_cm,
+                             int32_t nx, int32_t ny, int method, const int32_t* qx_cm,
+                             const int32_t* qy_cm, int64_t m, float* out, int8_t* how_out,
+                             void* cuda_stream);
+
+/* The same at every node of an output grid (ox0, oy0, ocell even, onx, ony),
+ * written row-major to out (device, onx*ony float32); how_out as above. The
+ * paper's row-filling tests (Sec. IV, Grid A) are the output grid offset by
+ * half a cell in y: the points halfway between successive rows. */
+bg_status bg_resample_grid(const float* src, int32_t x0_cm, int32_t y0_cm, int32_t cell_cm,
+                           int32_t nx, int32_t ny, int method, int32_t ox0_cm, int32_t oy0_cm,
+                           int32_t ocell_cm, int32_t onx, int32_t ony, float* out,
+                           int8_t* how_out, void* cuda_stream);
+
 /* ---------------------------------------------------------------- serving */
 
 /* A gridding request for bg_submit. Inputs and outputs are HOST memory; the

@@ -28,7 +28,8 @@ __all__ = [
     "version", "launch_count", "profile_enable", "profile_read", "ctx_create", "ctx_destroy",
     "ctx_device_bytes", "grid_create", "grid_destroy",
     "soundings_upload", "soundings_info", "soundings_destroy", "interp_idw", "interp_okrige",
-    "interp_idw_points", "interp_okrige_points",
+    "interp_idw_points", "interp_okrige_points", "BILINEAR", "CATMULL_ROM", "resample_points",
+    "resample_grid",
     "variogram", "interp_idw_noalloc", "submit", "poll", "wait", "cancel", "serve_stats",
     "serve_shutdown", "Request", "Result", "Batch", "batch_create", "batch_run", "batch_tune",
     "batch_set_cell_target", "batch_status", "batch_destroy",
@@ -211,6 +212,42 @@ def interp_okrige_points(s, qx_cm, qy_cm, k: int, vgm: Variogram, depth_out, var
     check(_lib().bg_interp_okrige_points(s, _ptr(qx_cm), _ptr(qy_cm), m, k, ctypes.byref(vgm),
                                          _ptr(depth_out), _ptr(var_out), _ptr(nbr_out),
                                          _stream(stream, depth_out)), "bg_interp_okrige_points")
+
+
+BILINEAR = 0
+CATMULL_ROM = 1
+
+
+def resample_points(src, grid_spec, method: int, qx_cm, qy_cm, out, how_out=None,
+                    stream=None) -> None:
+    """Bilinear / Catmull-Rom of a regular grid (device float32 [ny * nx], NaN =
+    missing; grid_spec = (x0_cm, y0_cm, cell_cm, nx, ny)) at query points."""
+    m = _check_points(qx_cm, qy_cm, out)
+    _check_dtype(src, "float32")
+    if how_out is not None:
+        _check_dtype(how_out, "int8")
+    x0, y0, cell, nx, ny = (int(v) for v in grid_spec)
+    if int(src.shape[0]) != nx * ny:
+        raise ValueError("src must hold nx * ny values")
+    check(_lib().bg_resample_points(_ptr(src), x0, y0, cell, nx, ny, int(method), _ptr(qx_cm),
+                                    _ptr(qy_cm), m, _ptr(out), _ptr(how_out),
+                                    _stream(stream, out)), "bg_resample_points")
+
+
+def resample_grid(src, grid_spec, method: int, out_spec, out, how_out=None, stream=None) -> None:
+    """Bilinear / Catmull-Rom of a regular grid at every node of the output grid
+    out_spec = (x0_cm, y0_cm, cell_cm, nx, ny), row-major into out."""
+    _check_dtype(src, "float32")
+    _check_dtype(out, "float32")
+    if how_out is not None:
+        _check_dtype(how_out, "int8")
+    x0, y0, cell, nx, ny = (int(v) for v in grid_spec)
+    ox0, oy0, ocell, onx, ony = (int(v) for v in out_spec)
+    if int(src.shape[0]) != nx * ny or int(out.shape[0]) < onx * ony:
+        raise ValueError("src must hold nx * ny values and out onx * ony")
+    check(_lib().bg_resample_grid(_ptr(src), x0, y0, cell, nx, ny, int(method), ox0, oy0, ocell,
+                                  onx, ony, _ptr(out), _ptr(how_out), _stream(stream, out)),
+          "bg_resample_grid")
 
 
 def interp_idw_noalloc(x_cm, y_cm, z_m, grid_spec, k: int, power: float, depth_out,

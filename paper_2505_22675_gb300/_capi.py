@@ -91,6 +91,12 @@ _SIGNATURES = {
                              ctypes.c_int),
     "bg_interp_okrige_points": ([P, P, P, ctypes.c_int64, ctypes.c_int, ctypes.POINTER(Variogram),
                                  P, P, P, P], ctypes.c_int),
+    "bg_resample_points": ([P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                            ctypes.c_int32, ctypes.c_int, P, P, ctypes.c_int64, P, P, P],
+                           ctypes.c_int),
+    "bg_resample_grid": ([P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                          ctypes.c_int32, ctypes.c_int, ctypes.c_int32, ctypes.c_int32,
+                          ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P, P, P], ctypes.c_int),
     "bg_submit": ([P, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
     "bg_poll": ([P, ctypes.c_uint64, ctypes.POINTER(Result)], ctypes.c_int),
     "bg_wait": ([P, ctypes.c_uint64, ctypes.c_int, ctypes.POINTER(Result)], ctypes.c_int),

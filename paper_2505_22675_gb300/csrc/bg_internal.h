@@ -193,6 +193,14 @@ bg_status launch_idw(const bg_soundings_s* s, const GridView& g, int k, float po
 bg_status launch_okrige(const bg_soundings_s* s, const GridView& g, int k, const OkParams& p,
                         float* depth, float* var, int32_t* nbr, cudaStream_t st);
 
+// Gridded input (bilinear / Catmull-Rom) at query points or output-grid nodes;
+// no allocation.
+bg_status launch_resample_points(const float* src, const GridView& g, int method,
+                                 const int32_t* qx, const int32_t* qy, int64_t m, float* out,
+                                 int8_t* how, cudaStream_t st);
+bg_status launch_resample_grid(const float* src, const GridView& g, int method, const GridView& o,
+                               float* out, int8_t* how, cudaStream_t st);
+
 // The same at a list of query points.
 bg_status launch_idw_points(const bg_soundings_s* s, const PointsView& q, int k, float power,
                             float* depth, int32_t* nbr, cudaStream_t st);

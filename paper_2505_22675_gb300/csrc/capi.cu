@@ -404,4 +404,43 @@ bg_status bg_interp_okrige_points(bg_soundings_t s, const int32_t* qx_cm, const 
                                 (cudaStream_t)cuda_stream);
 }
 
+static bg_status check_source(const float* src, int32_t x0, int32_t y0, int32_t cell, int32_t nx,
+                              int32_t ny, int method) {
+    BG_REQUIRE(src, "src is NULL");
+    BG_REQUIRE(cell > 0 && cell % 2 == 0, "cell_cm must be even and > 0");
+    BG_REQUIRE(nx >= 2 && ny >= 2, "the source grid needs at least 2 x 2 nodes");
+    BG_REQUIRE(grid_in_range(x0, y0, cell, nx, ny), "source nodes must lie in (-2^30, 2^30) cm");
+    BG_REQUIRE(method == BG_RESAMPLE_BILINEAR || method == BG_RESAMPLE_CATMULL_ROM,
+               "unknown resampling method");
+    return BG_OK;
+}
+
+bg_status bg_resample_points(const float* src, int32_t x0_cm, int32_t y0_cm, int32_t cell_cm,
+                             int32_t nx, int32_t ny, int method, const int32_t* qx_cm,
+                             const int32_t* qy_cm, int64_t m, float* out, int8_t* how_out,
+                             void* cuda_stream) {
+    bg_status rc = check_source(src, x0_cm, y0_cm, cell_cm, nx, ny, method);
+    if (rc != BG_OK) return rc;
+    BG_REQUIRE(m >= 0 && m < ((int64_t)1 << 40), "m must be in [0, 2^40)");
+    BG_REQUIRE(m == 0 || (qx_cm && qy_cm && out), "NULL query or output pointer");
+    return launch_resample_points(src, GridView{x0_cm, y0_cm, cell_cm, nx, ny}, method, qx_cm,
+                                  qy_cm, m, out, how_out, (cudaStream_t)cuda_stream);
+}
+
+bg_status bg_resample_grid(const float* src, int32_t x0_cm, int32_t y0_cm, int32_t cell_cm,
+                           int32_t nx, int32_t ny, int method, int32_t ox0_cm, int32_t oy0_cm,
+                           int32_t ocell_cm, int32_t onx, int32_t ony, float* out,
+                           int8_t* how_out, void* cuda_stream) {
+    bg_status rc = check_source(src, x0_cm, y0_cm, cell_cm, nx, ny, method);
+    if (rc != BG_OK) return rc;
+    BG_REQUIRE(out, "out is NULL");
+    BG_REQUIRE(ocell_cm > 0 && ocell_cm % 2 == 0, "output cell_cm must be even and > 0");
+    BG_REQUIRE(onx > 0 && ony > 0, "output nx, ny must be > 0");
+    BG_REQUIRE(grid_in_range(ox0_cm, oy0_cm, ocell_cm, onx, ony),
+               "output nodes must lie in (-2^30, 2^30) cm");
+    return launch_resample_grid(src, GridView{x0_cm, y0_cm, cell_cm, nx, ny}, method,
+                                GridView{ox0_cm, oy0_cm, ocell_cm, onx, ony}, out, how_out,
+                                (cudaStream_t)cuda_stream);
+}
+
 }  // extern "C"

@@ -1,0 +1,250 @@
+// Gridded input: bilinear (Sec. III-A) and Catmull-Rom (Sec. III-B)
+// resampling of a regular grid at query points or at the nodes of another
+// grid.
+//
+// Each query finds the lattice cell that holds it (exact integer
+// arithmetic: index i and remainder r in [0, cell] along each axis) and
+// reads the 2 x 2 (bilinear) or 4 x 4 (Catmull-Rom, edge nodes repeated)
+// nodes around it. A node is needed when its weight is not zero: a query on
+// a node line (r = 0 or r = cell) needs only that line. A needed NaN node
+// gives NaN for bilinear, which has no fallback, and sends Catmull-Rom to
+// bilinear. Sums are taken as anomalies from one needed node, so at depths of
+// thousands of metres only the final add rounds at that magnitude.
+//
+// A thread takes 4 queries 256 apart and reads the needed stencil nodes of
+// all four with predicated loads, so they overlap; a warp takes 32
+// neighbouring queries, so the source rows it reads are contiguous and
+// shared through L1. The work is a gather bounded by HBM: 4 B per output
+// (+ 8 B of coordinates for point lists), plus one read of the source grid.
+#include <algorithm>
+#include <cmath>
+
+#include "bg_internal.h"
+
+namespace bg {
+namespace {
+
+struct Src {
+    const float* v;
+    int32_t cx0, cy0;  // first node centre (cm)
+    int32_t cell, nx, ny;
+};
+
+// Position of a query along one axis of the node lattice: cell index i in
+// [0, n - 2], remainder r = u - i * cell in [0, cell] (u: offset from the
+// first node centre), and whether u lies inside the hull [0, (n-1) cell].
+// Outside, i = r = 0 so that every load the caller makes stays in bounds.
+struct Axis {
+    int i, r;
+    bool in;
+};
+
+__device__ __forceinline__ Axis axis_of(int64_t u, int cell, int n) {
+    Axis a;
+    a.in = u >= 0 && u <= (int64_t)(n - 1) * cell;
+    const unsigned uu = a.in ? (unsigned)u : 0u;  // < 2^31: node centres lie in (-2^30, 2^30)
+    unsigned q = uu / (unsigned)cell;
+    if (q > (unsigned)(n - 2)) q = (unsigned)(n - 2);
+    a.i = (int)q;
+    a.r = (int)(uu - q * (unsigned)cell);
+    return a;
+}
+
+// Which of the stencil points P0..P3 (nodes i-1 .. i+2) carry weight: all four
+// inside the cell, only P1 on the near node line, only P2 on the far one.
+__device__ __forceinline__ bool needed(const Axis& a, int cell, int k) {
+    return a.r == 0 ? k == 1 : (a.r == cell ? k == 2 : true);
+}
+
+// Bilinear (Sec. III-A) from the corner values; corners whose weight is zero
+// must come in as 0 (a NaN there does not enter), and a needed NaN corner
+// propagates through its term. Anomalies from a needed corner.
+__device__ __forceinline__ float bilinear_from(int cell, const Axis& ax, const Axis& ay, float q00,
+                                               float q10, float q01, float q11) {
+    const float t = (float)ax.r / (float)cell, u = (float)ay.r / (float)cell;
+    const bool x0 = ax.r != cell, y0 = ay.r != cell;
+    const float ref = x0 ? (y0 ? q00 : q01) : (y0 ? q10 : q11);
+    const float a = fmaf(1.0f - t, (1.0f - u) * (q00 - ref),
+                         fmaf(t, (1.0f - u) * (q10 - ref),
+                              fmaf(1.0f - t, u * (q01 - ref), t * u * (q11 - ref))));
+    return ref + a;
+}
+
+// Catmull-Rom weights of P0..P3 at t (Sec. III-B, C(t) expanded per point)
+__device__ __forceinline__ void cr_weights(float t, float (&w)[4]) {
+    const float t2 = t * t, t3 = t2 * t;
+    w[0] = 0.5f * (-t + 2.0f * t2 - t3);
+    w[1] = 0.5f * (2.0f - 5.0f * t2 + 3.0f * t3);
+    w[2] = 0.5f * (t + 4.0f * t2 - 3.0f * t3);
+    w[3] = 0.5f * (t3 - t2);
+}
+
+// One query from its two axes. rows[b] points at source row j - 1 + b
+// (clamped into the grid; bilinear uses rows[1] and rows[2]). Only the
+// needed stencil nodes are read (predicated loads, no branches), so the loads
+// of a thread's queries overlap. how: 0 by the method, 1 by the bilinear
+// fallback, 2 no value.
+template <int kMethod>
+__device__ __forceinline__ float resample_at(const Src& s, const Axis& ax, const Axis& ay,
+                                             const float* const (&rows)[4], int8_t& how) {
+    float f;
+    const int i = ax.i;
+    if constexpr (kMethod == BG_RESAMPLE_CATMULL_ROM) {
+        int col[4];
+        bool nx_[4], ny_[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            col[a] = min(max(i - 1 + a, 0), s.nx - 1);
+            nx_[a] = needed(ax, s.cell, a);
+            ny_[a] = needed(ay, s.cell, a);
+        }
+        float P[4][4];
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+#pragma unroll
+            for (int a = 0; a < 4; ++a) P[b][a] = (nx_[a] && ny_[b]) ? __ldg(rows[b] + col[a]) : 0.0f;
+        const float ref = P[ay.r == s.cell ? 2 : 1][ax.r == s.cell ? 2 : 1];
+        float wx[4], wy[4];
+        cr_weights((float)ax.r / (float)s.cell, wx);
+        cr_weights((float)ay.r / (float)s.cell, wy);
+        float acc = 0.0f;
+        bool nan = false;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            float r = 0.0f;
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                const bool need = nx_[a] && ny_[b];
+                nan |= need && isnan(P[b][a]);
+                r = need ? fmaf(wx[a], P[b][a] - ref, r) : r;
+            }
+            acc = ny_[b] ? fmaf(wy[b], r, acc) : acc;
+        }
+        if (!nan) {
+            f = ref + acc;
+            how = 0;
+        } else {
+            // the bilinear corners are stencil nodes (1,1), (2,1), (1,2), (2,2)
+            // and were read exactly when needed by bilinear too
+            f = bilinear_from(s.cell, ax, ay, P[1][1], P[1][2], P[2][1], P[2][2]);
+            how = isnan(f) ? 2 : 1;
+        }
+    } else {
+        const bool x0 = ax.r != s.cell, x1 = ax.r != 0, y0 = ay.r != s.cell, y1 = ay.r != 0;
+        const float q00 = (x0 && y0) ? __ldg(rows[1] + i) : 0.0f;
+        const float q10 = (x1 && y0) ? __ldg(rows[1] + i + 1) : 0.0f;
+        const float q01 = (x0 && y1) ? __ldg(rows[2] + i) : 0.0f;
+        const float q11 = (x1 && y1) ? __ldg(rows[2] + i + 1) : 0.0f;
+        f = bilinear_from(s.cell, ax, ay, q00, q10, q01, q11);
+        how = isnan(f) ? 2 : 0;
+    }
+    if (!(ax.in && ay.in)) {
+        how = 2;
+        f = __int_as_float(0x7fc00000);
+    }
+    return f;
+}
+
+__device__ __forceinline__ void row_ptrs(const Src& s, int j, const float* (&rows)[4]) {
+#pragma unroll
+    for (int b = 0; b < 4; ++b) rows[b] = s.v + (int64_t)min(max(j - 1 + b, 0), s.ny - 1) * s.nx;
+}
+
+constexpr int kThreads = 256;
+constexpr int kPer = 4;  // outputs per thread, kThreads apart: every access stays coalesced
+
+// Queries past the end are computed on a clamped index and not stored, so
+// that no load depends on a branch and the queries' loads overlap.
+template <int kMethod>
+__global__ void __launch_bounds__(kThreads) k_resample_pts(Src s, const int32_t* __restrict__ qx,
+                                                           const int32_t* __restrict__ qy,
+                                                           int64_t m, float* __restrict__ out,
+                                                           int8_t* __restrict__ how_out) {
+    for (int64_t base = (int64_t)blockIdx.x * kThreads * kPer; base < m;
+         base += (int64_t)gridDim.x * kThreads * kPer) {
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            const int64_t p = base + k * kThreads + threadIdx.x;
+            const int64_t pc = p < m ? p : m - 1;
+            const Axis ax = axis_of((int64_t)__ldg(qx + pc) - s.cx0, s.cell, s.nx);
+            const Axis ay = axis_of((int64_t)__ldg(qy + pc) - s.cy0, s.cell, s.ny);
+            const float* rows[4];
+            row_ptrs(s, ay.i, rows);
+            int8_t how;
+            const float f = resample_at<kMethod>(s, ax, ay, rows, how);
+            if (p < m) {
+                out[p] = f;
+                if (how_out) how_out[p] = how;
+            }
+        }
+    }
+}
+
+// output grid: block b takes row b / chunks and kThreads * kPer columns of
+// it; the row's position along y and its source rows are the block's
+template <int kMethod>
+__global__ void __launch_bounds__(kThreads) k_resample_grid(Src s, GridView o, int chunks,
+                                                            float* __restrict__ out,
+                                                            int8_t* __restrict__ how_out) {
+    const int row = blockIdx.x / chunks;
+    const int c0 = (blockIdx.x - row * chunks) * kThreads * kPer + threadIdx.x;
+    const Axis ay = axis_of((int64_t)o.y0 + (int64_t)row * o.cell + o.cell / 2 - s.cy0, s.cell, s.ny);
+    const float* rows[4];
+    row_ptrs(s, ay.i, rows);
+    const int64_t ux0 = (int64_t)o.x0 + o.cell / 2 - s.cx0;
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        const int c = c0 + k * kThreads;
+        const int cc = c < o.nx ? c : o.nx - 1;
+        const Axis ax = axis_of(ux0 + (int64_t)cc * o.cell, s.cell, s.nx);
+        int8_t how;
+        const float f = resample_at<kMethod>(s, ax, ay, rows, how);
+        if (c < o.nx) {
+            const int64_t p = (int64_t)row * o.nx + c;
+            out[p] = f;
+            if (how_out) how_out[p] = how;
+        }
+    }
+}
+
+}  // namespace
+
+bg_status launch_resample_points(const float* src, const GridView& g, int method,
+                                 const int32_t* qx, const int32_t* qy, int64_t m, float* out,
+                                 int8_t* how, cudaStream_t st) {
+    if (m == 0) return BG_OK;
+    const Src s{src, g.x0 + g.cell / 2, g.y0 + g.cell / 2, g.cell, g.nx, g.ny};
+    const int64_t blocks =
+        std::min<int64_t>((m + kThreads * kPer - 1) / (kThreads * kPer), (int64_t)152 * 64);
+    if (method == BG_RESAMPLE_CATMULL_ROM)
+        k_resample_pts<BG_RESAMPLE_CATMULL_ROM><<<(unsigned)blocks, kThreads, 0, st>>>(s, qx, qy, m,
+                                                                                     out, how);
+    else
+        k_resample_pts<BG_RESAMPLE_BILINEAR><<<(unsigned)blocks, kThreads, 0, st>>>(s, qx, qy, m,
+                                                                                  out, how);
+    note_launches(1);
+    BG_CUDA(cudaGetLastError());
+    return BG_OK;
+}
+
+bg_status launch_resample_grid(const float* src, const GridView& g, int method, const GridView& o,
+                               float* out, int8_t* how, cudaStream_t st) {
+    const Src s{src, g.x0 + g.cell / 2, g.y0 + g.cell / 2, g.cell, g.nx, g.ny};
+    const int chunks = (o.nx + kThreads * kPer - 1) / (kThreads * kPer);
+    const int64_t blocks = (int64_t)chunks * o.ny;
+    if (blocks >= ((int64_t)1 << 31)) {
+        set_error("output grid too large for one launch");
+        return BG_ERR_INVALID_ARG;
+    }
+    if (method == BG_RESAMPLE_CATMULL_ROM)
+        k_resample_grid<BG_RESAMPLE_CATMULL_ROM><<<(unsigned)blocks, kThreads, 0, st>>>(s, o, chunks,
+                                                                                      out, how);
+    else
+        k_resample_grid<BG_RESAMPLE_BILINEAR><<<(unsigned)blocks, kThreads, 0, st>>>(s, o, chunks,
+                                                                                   out, how);
+    note_launches(1);
+    BG_CUDA(cudaGetLastError());
+    return BG_OK;
+}
+
+}  // namespace bg

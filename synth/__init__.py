@@ -278,6 +278,12 @@ class HoleGrid:
         z[self.holes] = np.nan
         return z
 
+    def with_frac(self, frac: float, seed: int) -> "HoleGrid":
+        """The same depths with another random removal (seeded)."""
+        m = self.grid.m
+        holes = np.sort(_rng(seed).choice(m, size=int(round(frac * m)), replace=False))
+        return HoleGrid(self.grid, self.z_full, holes.astype(np.int64), frac, seed)
+
 
 def _lattice_field(x_m: np.ndarray, y_m: np.ndarray, table: np.ndarray, cut_sigmas=5.0):
     """Bump field on the lattice x_m (columns) by y_m (rows), both ascending and

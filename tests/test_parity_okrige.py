@@ -104,6 +104,35 @@ def test_coincident_nodes_duplicates_and_nan():
         assert abs(float(d[m]) - float(z[i])) <= 1e-3 and abs(float(v[m])) <= 2.5e-5
 
 
+def _lattice_with_duplicates(seed):
+    rng = np.random.default_rng(seed)
+    xs = rng.integers(0, 40, 900) * 100 + 50
+    ys = rng.integers(0, 40, 900) * 100 + 50
+    x = np.concatenate([xs, xs[:100]]).astype(np.int32)
+    y = np.concatenate([ys, ys[:100]]).astype(np.int32)
+    z = (3500 + 0.01 * x / 100 + rng.normal(0, 0.5, x.size)).astype(np.float32)
+    z[rng.random(x.size) < 0.1] = np.nan
+    return synth.Workload(x, y, z, synth.GridSpec(0, 0, 100, 40, 40), "coinc", {})
+
+
+@pytest.mark.parametrize("k", [32, 16, 5, 1])
+def test_without_neighbour_output_the_solve_orders_the_ids(k):
+    # without nbr_out the k-NN hands the ids over unsorted and the solve puts
+    # them in (d2, index) order itself: results bitwise those with nbr_out
+    for w in (synth.tile(seed=12, n=8000, side_cm=30_000, cell_cm=200),
+              _lattice_with_duplicates(13)):
+        lib = Lib(w.x_cm, w.y_cm, w.z_m, w.grid)
+        try:
+            d1, v1, _ = lib.okrige(k, **SPH, want_nbr=True)
+            d2, v2, _ = lib.okrige(k, **SPH, want_nbr=False)
+        finally:
+            lib.close()
+        assert np.array_equal(d1.view(np.uint32), d2.view(np.uint32))
+        assert np.array_equal(v1.view(np.uint32), v2.view(np.uint32))
+        rd, rv, _ = _oracle(w, k, **SPH)
+        assert_okrige(d2, v2, rd, rv, SPH["nugget"])
+
+
 def test_fewer_soundings_than_k_and_none_valid():
     x = np.array([0, 500, 900, 40], np.int32)
     y = np.array([0, 200, -300, 700], np.int32)

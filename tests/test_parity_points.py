@@ -48,16 +48,16 @@ class PLib:
         t.cuda.synchronize()
         return d.cpu().numpy(), nb.cpu().numpy().reshape(m, k)
 
-    def okrige(self, qx, qy, k, vgm=VGM):
+    def okrige(self, qx, qy, k, vgm=VGM, want_nbr=True):
         t = self.torch
         m = len(qx)
         dx, dy = self._q(qx, qy)
         d = t.full((m,), -7.0, device=self.dev)
         v = t.full((m,), -7.0, device=self.dev)
-        nb = t.full((m * k,), -9, dtype=t.int32, device=self.dev)
+        nb = t.full((m * k,), -9, dtype=t.int32, device=self.dev) if want_nbr else None
         self.bg.interp_okrige_points(self.s, dx, dy, k, self.bg.variogram(*vgm), d, v, nb)
         t.cuda.synchronize()
-        return d.cpu().numpy(), v.cpu().numpy(), nb.cpu().numpy().reshape(m, k)
+        return d.cpu().numpy(), v.cpu().numpy(), (nb.cpu().numpy().reshape(m, k) if want_nbr else None)
 
     def close(self):
         self.bg.soundings_destroy(self.s)
@@ -95,7 +95,7 @@ def test_hole_filling_in_scan_order_and_shuffled():
         d, od, ov = _check(lib, s.x_cm, s.y_cm, s.z_m, qx, qy)
         perm = np.random.default_rng(0).permutation(qx.size)
         d2, _ = lib.idw(qx[perm], qy[perm], 16)
-        od2, ov2, _ = lib.okrige(qx[perm], qy[perm], 32)
+        od2, ov2, _ = lib.okrige(qx[perm], qy[perm], 32, want_nbr=False)  # ids unsorted
         assert np.array_equal(d2.view(np.uint32), d[perm].view(np.uint32))
         assert np.array_equal(od2.view(np.uint32), od[perm].view(np.uint32))
         assert np.array_equal(ov2.view(np.uint32), ov[perm].view(np.uint32))
