@@ -28,7 +28,15 @@ struct Src {
     const float* v;
     int32_t cx0, cy0;  // first node centre (cm)
     int32_t cell, nx, ny;
+    float inv_cell;    // 1 / cell
 };
+
+// r / cell for r in [0, cell], exactly 0 and 1 at the ends (a multiply by the
+// reciprocal elsewhere: one rounding more than a division, far below the
+// tolerance of a depth)
+__device__ __forceinline__ float frac_of(int r, const Src& s) {
+    return r == s.cell ? 1.0f : (float)r * s.inv_cell;
+}
 
 // Position of a query along one axis of the node lattice: cell index i in
 // [0, n - 2], remainder r = u - i * cell in [0, cell] (u: offset from the
@@ -59,10 +67,10 @@ __device__ __forceinline__ bool needed(const Axis& a, int cell, int k) {
 // Bilinear (Sec. III-A) from the corner values; corners whose weight is zero
 // must come in as 0 (a NaN there does not enter), and a needed NaN corner
 // propagates through its term. Anomalies from a needed corner.
-__device__ __forceinline__ float bilinear_from(int cell, const Axis& ax, const Axis& ay, float q00,
-                                               float q10, float q01, float q11) {
-    const float t = (float)ax.r / (float)cell, u = (float)ay.r / (float)cell;
-    const bool x0 = ax.r != cell, y0 = ay.r != cell;
+__device__ __forceinline__ float bilinear_from(const Src& s, const Axis& ax, const Axis& ay,
+                                               float q00, float q10, float q01, float q11) {
+    const float t = frac_of(ax.r, s), u = frac_of(ay.r, s);
+    const bool x0 = ax.r != s.cell, y0 = ay.r != s.cell;
     const float ref = x0 ? (y0 ? q00 : q01) : (y0 ? q10 : q11);
     const float a = fmaf(1.0f - t, (1.0f - u) * (q00 - ref),
                          fmaf(t, (1.0f - u) * (q10 - ref),
@@ -105,8 +113,8 @@ __device__ __forceinline__ float resample_at(const Src& s, const Axis& ax, const
             for (int a = 0; a < 4; ++a) P[b][a] = (nx_[a] && ny_[b]) ? __ldg(rows[b] + col[a]) : 0.0f;
         const float ref = P[ay.r == s.cell ? 2 : 1][ax.r == s.cell ? 2 : 1];
         float wx[4], wy[4];
-        cr_weights((float)ax.r / (float)s.cell, wx);
-        cr_weights((float)ay.r / (float)s.cell, wy);
+        cr_weights(frac_of(ax.r, s), wx);
+        cr_weights(frac_of(ay.r, s), wy);
         float acc = 0.0f;
         bool nan = false;
 #pragma unroll
@@ -126,7 +134,7 @@ __device__ __forceinline__ float resample_at(const Src& s, const Axis& ax, const
         } else {
             // the bilinear corners are stencil nodes (1,1), (2,1), (1,2), (2,2)
             // and were read exactly when needed by bilinear too
-            f = bilinear_from(s.cell, ax, ay, P[1][1], P[1][2], P[2][1], P[2][2]);
+            f = bilinear_from(s, ax, ay, P[1][1], P[1][2], P[2][1], P[2][2]);
             how = isnan(f) ? 2 : 1;
         }
     } else {
@@ -135,7 +143,7 @@ __device__ __forceinline__ float resample_at(const Src& s, const Axis& ax, const
         const float q10 = (x1 && y0) ? __ldg(rows[1] + i + 1) : 0.0f;
         const float q01 = (x0 && y1) ? __ldg(rows[2] + i) : 0.0f;
         const float q11 = (x1 && y1) ? __ldg(rows[2] + i + 1) : 0.0f;
-        f = bilinear_from(s.cell, ax, ay, q00, q10, q01, q11);
+        f = bilinear_from(s, ax, ay, q00, q10, q01, q11);
         how = isnan(f) ? 2 : 0;
     }
     if (!(ax.in && ay.in)) {
@@ -213,7 +221,7 @@ bg_status launch_resample_points(const float* src, const GridView& g, int method
                                  const int32_t* qx, const int32_t* qy, int64_t m, float* out,
                                  int8_t* how, cudaStream_t st) {
     if (m == 0) return BG_OK;
-    const Src s{src, g.x0 + g.cell / 2, g.y0 + g.cell / 2, g.cell, g.nx, g.ny};
+    const Src s{src, g.x0 + g.cell / 2, g.y0 + g.cell / 2, g.cell, g.nx, g.ny, 1.0f / (float)g.cell};
     const int64_t blocks =
         std::min<int64_t>((m + kThreads * kPer - 1) / (kThreads * kPer), (int64_t)152 * 64);
     if (method == BG_RESAMPLE_CATMULL_ROM)
@@ -229,7 +237,7 @@ bg_status launch_resample_points(const float* src, const GridView& g, int method
 
 bg_status launch_resample_grid(const float* src, const GridView& g, int method, const GridView& o,
                                float* out, int8_t* how, cudaStream_t st) {
-    const Src s{src, g.x0 + g.cell / 2, g.y0 + g.cell / 2, g.cell, g.nx, g.ny};
+    const Src s{src, g.x0 + g.cell / 2, g.y0 + g.cell / 2, g.cell, g.nx, g.ny, 1.0f / (float)g.cell};
     const int chunks = (o.nx + kThreads * kPer - 1) / (kThreads * kPer);
     const int64_t blocks = (int64_t)chunks * o.ny;
     if (blocks >= ((int64_t)1 << 31)) {
