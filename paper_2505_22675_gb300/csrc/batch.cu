@@ -310,7 +310,7 @@ __global__ void __launch_bounds__(kItemThreads) k_batch_knn(
 // descriptor is staged in shared memory so its fields are read where needed
 // instead of being held in registers across the solve
 template <int K>
-__global__ void __launch_bounds__(kSolveWarps * 32, 6) k_batch_solve(
+__global__ void __launch_bounds__(kSolveWarps * 32, kSolveBlocksPerSM) k_batch_solve(
     const TileDesc* __restrict__ td, const int* __restrict__ tiles, int nt,
     const int64_t* __restrict__ off, int64_t items, unsigned long long* __restrict__ ctr,
     const int4* __restrict__ orig, const int4* __restrict__ rec, const int* __restrict__ cell_start,

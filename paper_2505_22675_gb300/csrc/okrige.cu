@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(128) k_knn_ids_wide(HashView h, GridView g, in
 }
 
 template <int K>
-__global__ void __launch_bounds__(kSolveWarps * 32) k_okrige_solve(
+__global__ void __launch_bounds__(kSolveWarps * 32, kSolveBlocksPerSM) k_okrige_solve(
     HashView h, GridView g, int k, OkParams p, int64_t node0, int64_t nodes,
     const int32_t* __restrict__ ids, float* __restrict__ depth, float* __restrict__ var) {
     __shared__ float smem[kSolveWarps * Geo<K>::WARP_FLOATS];
@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(128) k_knn_ids_pts_wide(HashView h, PointsView
 }
 
 template <int K>
-__global__ void __launch_bounds__(kSolveWarps * 32) k_okrige_solve_pts(
+__global__ void __launch_bounds__(kSolveWarps * 32, kSolveBlocksPerSM) k_okrige_solve_pts(
     HashView h, PointsView q, int k, OkParams p, int64_t p0, int64_t nodes,
     const int32_t* __restrict__ ids, float* __restrict__ depth, float* __restrict__ var) {
     __shared__ float smem[kSolveWarps * Geo<K>::WARP_FLOATS];

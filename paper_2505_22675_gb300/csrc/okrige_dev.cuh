@@ -14,14 +14,16 @@
 // A is symmetric positive definite for a conditionally negative definite
 // variogram (spherical and exponential are, in 2-D), so |A[r][c]| is bounded
 // by its largest diagonal entry. It is assembled once per entry straight into
-// a 30-bit fixed-point copy in shared memory (lower triangle), factored by
-// Cholesky in FP32 with each thread's rows in registers (thread t, slot s holds
-// row G*s + t, columns 0 .. G*(s+1)-1; pivots and column entries move between
-// the G threads by warp shuffles), and the factor is kept transposed in the
-// upper triangle for the back sweeps. One step of iterative refinement
-// follows: x is rounded to 24-bit fixed point x' (exact in FP32), the
-// residual b - A' x' is accumulated exactly in 64-bit integers, and the
-// correction reuses the factor. The weight sum closes in FP64:
+// a 30-bit fixed-point copy in shared memory (packed lower triangle), factored
+// by Cholesky in FP32 with each thread's rows in registers (thread t, slot s
+// holds row G*s + t, columns 0 .. G*(s+1)-1; pivots and column entries move
+// between the G threads by warp shuffles). The back sweeps also run on the
+// register rows, one column at a time with a group sum (no transposed copy of
+// the factor), so shared memory per system stays near 2.5 KB (K = 32) and,
+// with the registers held to 128, a GB300 SM keeps 16 warps resident. One
+// step of iterative refinement follows: x is rounded to 24-bit fixed point x'
+// (exact in FP32), the residual b - A' x' is accumulated exactly in 64-bit
+// integers, and the correction reuses the factor. The weight sum closes in FP64:
 // lambda_0 = 1 - sum(lambda'). Outputs:
 //     zhat    = z_0 + sum_a lambda_a (z_a - z_0)          (= sum lambda_i z_i)
 //     sigma^2 = lambda_0 gamma_00 + sum_a lambda_a gamma_a0 + mu.
@@ -42,18 +44,19 @@ namespace bg {
 constexpr int kR = 4;            // rows per thread
 constexpr int kSolveWarps = 2;   // warps per solve block
 constexpr int kRounds = 8;       // system batches per warp
+constexpr int kSolveBlocksPerSM = 8;  // launch bound: 16 warps resident (128 registers)
 
 template <int K>
 struct Geo {
     static constexpr int G = K / kR;                      // threads per system
     static constexpr int SYS = 32 / G;                    // systems per warp
     static constexpr int LEN = G * kR * (kR + 1) / 2;     // register floats of L
-    static constexpr int ROW = K + 1;                     // smem row stride (bank = row + col)
+    static constexpr int TRI = K * (K + 1) / 2;           // packed lower triangle of A
     static constexpr int TAB = K + 1;                     // neighbour table length
-    // per system: one K x (K+1) matrix (lower = fixed-point A, upper = factor
-    // transposed) and three neighbour tables; the stride is = G (mod 32) so
-    // that the G-thread groups of a warp cover all 32 banks
-    static constexpr int RAW = K * ROW + 3 * TAB;
+    // per system: the fixed-point A as a packed lower triangle (row r at
+    // r (r + 1) / 2), then the three neighbour tables; the stride is = G
+    // (mod 32) so that the G-thread groups of a warp spread over the banks
+    static constexpr int RAW = TRI + 3 * TAB;
     static constexpr int SYS_FLOATS = RAW + ((G - RAW % 32) + 32) % 32;
     static constexpr int WARP_FLOATS = SYS * SYS_FLOATS;
     static __host__ __device__ constexpr int off(int s) { return G * s * (s + 1) / 2; }
@@ -201,29 +204,33 @@ __device__ __forceinline__ void fwd_step(const float (&L)[Geo<K>::LEN], const fl
         if (G * (s + 1) - 1 > J && G * s + t > J) v[s] = fmaf(-L[Gm::off(s) + J], yj, v[s]);
 }
 
-// transposed sweep for column j = K-1-I of L^T x = y: the owner of row j
-// finishes x_j and broadcasts it; rows r < j subtract L[j][r] x_j, read from
-// the transposed copy of the factor at (r, j) in shared memory
+// back sweep for column J = K-1-I of L^T x = y in dot-product form: each
+// thread sums L[r][J] x_r over its solved rows r > J (its register rows of
+// L), the group adds the partial sums (xor shuffles), and the owner of row J
+// finishes x_J. No transposed copy of the factor is kept, which holds the
+// shared memory per system to the packed A and the tables.
 template <int K, int I>
-__device__ __forceinline__ void bwd_step(const float* Lt, const float (&dinv)[kR], float (&v)[kR],
-                                         int t, int gbase) {
+__device__ __forceinline__ void bwd_step(const float (&L)[Geo<K>::LEN], const float (&dinv)[kR],
+                                         float (&v)[kR], int t) {
     using Gm = Geo<K>;
     constexpr int G = Gm::G;
     constexpr int J = K - 1 - I;
     constexpr int SJ = J / G;
-    if (t == J % G) v[SJ] *= dinv[SJ];
-    const float xj = __shfl_sync(kFull, v[SJ], gbase + J % G);
+    float part = 0.0f;
 #pragma unroll
     for (int s = 0; s < kR; ++s)
-        if (G * s < J && G * s + t < J) v[s] = fmaf(-Lt[(G * s + t) * Gm::ROW + J], xj, v[s]);
+        if (G * (s + 1) - 1 > J) part = (G * s + t > J) ? fmaf(L[Gm::off(s) + J], v[s], part) : part;
+#pragma unroll
+    for (int o = 1; o < G; o <<= 1) part += __shfl_xor_sync(kFull, part, o);
+    if (t == J % G) v[SJ] = (v[SJ] - part) * dinv[SJ];
 }
 
 template <int K, int... J>
-__device__ __forceinline__ void chol_solve_seq(const float (&L)[Geo<K>::LEN], const float* Lt,
+__device__ __forceinline__ void chol_solve_seq(const float (&L)[Geo<K>::LEN],
                                                const float (&dinv)[kR], float (&v)[kR], int t,
                                                int gbase, std::integer_sequence<int, J...>) {
     (fwd_step<K, J>(L, dinv, v, t, gbase), ...);
-    (bwd_step<K, J>(Lt, dinv, v, t, gbase), ...);
+    (bwd_step<K, J>(L, dinv, v, t), ...);
 }
 
 // 2^e as a float (|e| <= 126)
@@ -248,13 +255,11 @@ __device__ __forceinline__ void okrige_solve_block(const HashView& h, const Grid
                                                    const int32_t* __restrict__ py = nullptr) {
     using Gm = Geo<K>;
     constexpr int G = Gm::G;
-    constexpr int ROW = Gm::ROW;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int grp = lane / G, t = lane % G, gbase = grp * G;
     float* sysmem = smem + warp * Gm::WARP_FLOATS + grp * Gm::SYS_FLOATS;
-    int* Aq = reinterpret_cast<int*>(sysmem);      // lower triangle: fixed-point A
-    float* Lt = sysmem;                             // strict upper triangle: L transposed
-    float* fx = sysmem + K * ROW;                   // x of neighbour n minus x of neighbour 0 (cm)
+    int* Aq = reinterpret_cast<int*>(sysmem);      // packed lower triangle: fixed-point A
+    float* fx = sysmem + Gm::TRI;                   // x of neighbour n minus x of neighbour 0 (cm)
     float* fy = fx + Gm::TAB;                       // y likewise
     float* tg = fy + Gm::TAB;                       // Gamma(neighbour of row r, neighbour 0)
     const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << gbase);
@@ -330,7 +335,7 @@ __device__ __forceinline__ void okrige_solve_block(const HashView& h, const Grid
                     v = (row && c + 1 < ke)
                             ? (grr + tg[c]) - gamma_pair_f(p, xr - fx[c + 1], yr - fy[c + 1])
                             : 0.0f;
-                Aq[r * ROW + c] = __float2int_rn(v * sa);
+                Aq[tri(r) + c] = __float2int_rn(v * sa);
             }
         }
         __syncwarp();
@@ -344,25 +349,16 @@ __device__ __forceinline__ void okrige_solve_block(const HashView& h, const Grid
             b[s] = (r + 1 < ke) ? (gr0[s] + g00) - g0r[s] : 0.0f;
 #pragma unroll
             for (int c = 0; c < G * (s + 1); ++c) {
-                const int q = Aq[c <= r ? r * ROW + c : 0];
+                const int q = Aq[c <= r ? tri(r) + c : 0];
                 L[Gm::off(s) + c] = c <= r ? (float)q * isa : 0.0f;
             }
         }
 
-        // factor in registers; L transposed into the upper triangle for the
-        // back sweeps (row r, column c < r goes to (c, r))
+        // factor in registers
         float dinv[kR];
 #pragma unroll
         for (int s = 0; s < kR; ++s) dinv[s] = 1.0f;
         chol_factor<K>(L, dinv, t, gbase, std::make_integer_sequence<int, K>{});
-#pragma unroll
-        for (int s = 0; s < kR; ++s) {
-            const int r = G * s + t;
-#pragma unroll
-            for (int c = 0; c < G * (s + 1); ++c)
-                if (c < r) Lt[c * ROW + r] = L[Gm::off(s) + c];
-        }
-        __syncwarp();
 
         // solve, one refinement step, solve again. The residual b - A' x' is
         // exact: x' is x rounded to 24-bit fixed point (representable in FP32),
@@ -373,7 +369,7 @@ __device__ __forceinline__ void okrige_solve_block(const HashView& h, const Grid
         for (int s = 0; s < kR; ++s) v[s] = b[s];
 #pragma unroll 1
         for (int pass = 0; pass < 2; ++pass) {
-            chol_solve_seq<K>(L, Lt, dinv, v, t, gbase, std::make_integer_sequence<int, K>{});
+            chol_solve_seq<K>(L, dinv, v, t, gbase, std::make_integer_sequence<int, K>{});
             if (pass == 1) {
 #pragma unroll
                 for (int s = 0; s < kR; ++s) x[s] += v[s];
@@ -403,7 +399,7 @@ __device__ __forceinline__ void okrige_solve_block(const HashView& h, const Grid
 #pragma unroll
                     for (int s = 0; s < kR; ++s) {
                         const int r = G * s + t;
-                        const int a = Aq[max(r, c) * ROW + min(r, c)];
+                        const int a = Aq[tri(max(r, c)) + min(r, c)];
                         acc[s] -= (long long)a * (long long)xc;
                     }
                 }

@@ -98,44 +98,77 @@ __device__ __forceinline__ float resample_at(const Src& s, const Axis& ax, const
     float f;
     const int i = ax.i;
     if constexpr (kMethod == BG_RESAMPLE_CATMULL_ROM) {
-        int col[4];
-        bool nx_[4], ny_[4];
+        if (ax.r == 0 || ax.r == s.cell) {
+            // on a node column (the row-filling shape): one column of the stencil,
+            // the same arithmetic as the general case with x weights (0, 1, 0, 0)
+            const int a = ax.r == 0 ? 1 : 2;
+            const int c = i - 1 + a;
+            bool ny_[4];
+            float P[4];
 #pragma unroll
-        for (int a = 0; a < 4; ++a) {
-            col[a] = min(max(i - 1 + a, 0), s.nx - 1);
-            nx_[a] = needed(ax, s.cell, a);
-            ny_[a] = needed(ay, s.cell, a);
-        }
-        float P[4][4];
+            for (int b = 0; b < 4; ++b) {
+                ny_[b] = needed(ay, s.cell, b);
+                P[b] = ny_[b] ? __ldg(rows[b] + c) : 0.0f;
+            }
+            const float ref = P[ay.r == s.cell ? 2 : 1];
+            float wy[4];
+            cr_weights(frac_of(ay.r, s), wy);
+            float acc = 0.0f;
+            bool nan = false;
 #pragma unroll
-        for (int b = 0; b < 4; ++b)
-#pragma unroll
-            for (int a = 0; a < 4; ++a) P[b][a] = (nx_[a] && ny_[b]) ? __ldg(rows[b] + col[a]) : 0.0f;
-        const float ref = P[ay.r == s.cell ? 2 : 1][ax.r == s.cell ? 2 : 1];
-        float wx[4], wy[4];
-        cr_weights(frac_of(ax.r, s), wx);
-        cr_weights(frac_of(ay.r, s), wy);
-        float acc = 0.0f;
-        bool nan = false;
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-            float r = 0.0f;
+            for (int b = 0; b < 4; ++b) {
+                nan |= ny_[b] && isnan(P[b]);
+                acc = ny_[b] ? fmaf(wy[b], P[b] - ref, acc) : acc;
+            }
+            if (!nan) {
+                f = ref + acc;
+                how = 0;
+            } else {
+                f = bilinear_from(s, ax, ay, a == 1 ? P[1] : 0.0f, a == 2 ? P[1] : 0.0f,
+                                  a == 1 ? P[2] : 0.0f, a == 2 ? P[2] : 0.0f);
+                how = isnan(f) ? 2 : 1;
+            }
+        } else {
+            int col[4];
+            bool nx_[4], ny_[4];
 #pragma unroll
             for (int a = 0; a < 4; ++a) {
-                const bool need = nx_[a] && ny_[b];
-                nan |= need && isnan(P[b][a]);
-                r = need ? fmaf(wx[a], P[b][a] - ref, r) : r;
+                col[a] = min(max(i - 1 + a, 0), s.nx - 1);
+                nx_[a] = needed(ax, s.cell, a);
+                ny_[a] = needed(ay, s.cell, a);
             }
-            acc = ny_[b] ? fmaf(wy[b], r, acc) : acc;
-        }
-        if (!nan) {
-            f = ref + acc;
-            how = 0;
-        } else {
-            // the bilinear corners are stencil nodes (1,1), (2,1), (1,2), (2,2)
-            // and were read exactly when needed by bilinear too
-            f = bilinear_from(s, ax, ay, P[1][1], P[1][2], P[2][1], P[2][2]);
-            how = isnan(f) ? 2 : 1;
+            float P[4][4];
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+                    P[b][a] = (nx_[a] && ny_[b]) ? __ldg(rows[b] + col[a]) : 0.0f;
+            const float ref = P[ay.r == s.cell ? 2 : 1][ax.r == s.cell ? 2 : 1];
+            float wx[4], wy[4];
+            cr_weights(frac_of(ax.r, s), wx);
+            cr_weights(frac_of(ay.r, s), wy);
+            float acc = 0.0f;
+            bool nan = false;
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                float r = 0.0f;
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    const bool need = nx_[a] && ny_[b];
+                    nan |= need && isnan(P[b][a]);
+                    r = need ? fmaf(wx[a], P[b][a] - ref, r) : r;
+                }
+                acc = ny_[b] ? fmaf(wy[b], r, acc) : acc;
+            }
+            if (!nan) {
+                f = ref + acc;
+                how = 0;
+            } else {
+                // the bilinear corners are stencil nodes (1,1), (2,1), (1,2), (2,2)
+                // and were read exactly when needed by bilinear too
+                f = bilinear_from(s, ax, ay, P[1][1], P[1][2], P[2][1], P[2][2]);
+                how = isnan(f) ? 2 : 1;
+            }
         }
     } else {
         const bool x0 = ax.r != s.cell, x1 = ax.r != 0, y0 = ay.r != s.cell, y1 = ay.r != 0;
