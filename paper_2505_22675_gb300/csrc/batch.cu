@@ -55,6 +55,7 @@ namespace {
 constexpr int kChunk = 4096;      // soundings per block in the per-sounding kernels
 constexpr int kBT = 256;          // threads of those kernels
 constexpr int kItemThreads = 128;
+constexpr int kBatchSolveBlocks = 8;  // solve blocks per claimed item: one atomic per 64 systems
 
 __device__ __forceinline__ int upper_tile(const int64_t* off, int T, int64_t v) {
     // largest t with off[t] <= v  (off ascending, off[0] = 0)
@@ -343,8 +344,10 @@ __global__ void __launch_bounds__(kSolveWarps * 32, kSolveBlocksPerSM) k_batch_s
         __syncthreads();
         const long long item = s_item;
         if (item >= items) break;
-        okrige_solve_block<K>(s_h, s_g, s_k, s_p, 0, (int64_t)s_g.nx * s_g.ny, s_ids, s_depth, s_var,
-                              item - __ldg(off + s_j), smem);
+        const int64_t b0 = (item - __ldg(off + s_j)) * kBatchSolveBlocks;
+        for (int b = 0; b < kBatchSolveBlocks; ++b)
+            okrige_solve_block<K>(s_h, s_g, s_k, s_p, 0, (int64_t)s_g.nx * s_g.ny, s_ids, s_depth,
+                                  s_var, b0 + b, smem);
         __syncthreads();  // the next item overwrites the staged descriptor
     }
 }
@@ -658,7 +661,7 @@ bg_status bg_batch_create(bg_ctx_t ctx, const bg_tile* tiles, int n_tiles, bg_ba
         if (gt[q].empty()) continue;
         bg_batch_s::Group G{Ks[q], (int)gt[q].size(), 0, (int*)(base + o_gt[q]),
                             (int64_t*)(base + o_go[q])};
-        const int sys_per_item = kSolveWarps * (32 / (Ks[q] / kR)) * kRounds;
+        const int sys_per_item = kSolveWarps * (32 / (Ks[q] / kR)) * kRounds * kBatchSolveBlocks;
         std::vector<int64_t> go(gt[q].size() + 1, 0);
         for (size_t j = 0; j < gt[q].size(); ++j) {
             const TileDesc& d = b->host_desc[gt[q][j]];

@@ -43,7 +43,7 @@ namespace bg {
 
 constexpr int kR = 4;            // rows per thread
 constexpr int kSolveWarps = 2;   // warps per solve block
-constexpr int kRounds = 8;       // system batches per warp
+constexpr int kRounds = 1;       // system batches per warp (one: more, shorter blocks balance best)
 constexpr int kSolveBlocksPerSM = 8;  // launch bound: 16 warps resident (128 registers)
 
 template <int K>
@@ -347,6 +347,10 @@ __device__ __forceinline__ void okrige_solve_block(const HashView& h, const Grid
         for (int s = 0; s < kR; ++s) {
             const int r = G * s + t;
             b[s] = (r + 1 < ke) ? (gr0[s] + g00) - g0r[s] : 0.0f;
+            // the tables are free after assembly: keep the row's output terms
+            // there rather than in registers through the solve
+            fx[r + 1] = zr[s] - z0;
+            fy[r + 1] = g0r[s] - gr0[s];
 #pragma unroll
             for (int c = 0; c < G * (s + 1); ++c) {
                 const int q = Aq[c <= r ? tri(r) + c : 0];
@@ -415,8 +419,8 @@ __device__ __forceinline__ void okrige_solve_block(const HashView& h, const Grid
             const bool row = G * s + t + 1 < ke;
             const float lam = row ? x[s] : 0.0f;
             ps += lam;
-            pz = fmaf(lam, zr[s] - z0, pz);
-            pv = fmaf(lam, g0r[s] - gr0[s], pv);
+            pz = fmaf(lam, fx[G * s + t + 1], pz);  // z_a - z_0
+            pv = fmaf(lam, fy[G * s + t + 1], pv);  // gamma_0a - Gamma_a0
         }
         double wsum = (double)ps;
 #pragma unroll
