@@ -320,7 +320,7 @@ __global__ void __launch_bounds__(kSolveWarps * 32, kBatchSolveBlocksPerSM) k_ba
     const int64_t* __restrict__ off, int64_t items, unsigned long long* __restrict__ ctr,
     const int4* __restrict__ orig, const int4* __restrict__ rec, const int* __restrict__ cell_start,
     const int* __restrict__ sat) {
-    __shared__ float smem[kSolveWarps * Geo<K>::WARP_FLOATS];
+    __shared__ __align__(16) float smem[kSolveWarps * Geo<K>::WARP_FLOATS];
     __shared__ long long s_item;
     __shared__ int s_j;
     __shared__ HashView s_h;

@@ -49,7 +49,7 @@ template <int K>
 __global__ void __launch_bounds__(kSolveWarps * 32, kSolveBlocksPerSM) k_okrige_solve(
     HashView h, GridView g, int k, OkParams p, int64_t node0, int64_t nodes,
     const int32_t* __restrict__ ids, float* __restrict__ depth, float* __restrict__ var) {
-    __shared__ float smem[kSolveWarps * Geo<K>::WARP_FLOATS];
+    __shared__ __align__(16) float smem[kSolveWarps * Geo<K>::WARP_FLOATS];
     okrige_solve_block<K>(h, g, k, p, node0, nodes, ids, depth, var, blockIdx.x, smem);
 }
 
@@ -142,7 +142,7 @@ template <int K>
 __global__ void __launch_bounds__(kSolveWarps * 32, kSolveBlocksPerSM) k_okrige_solve_pts(
     HashView h, PointsView q, int k, OkParams p, int64_t p0, int64_t nodes,
     const int32_t* __restrict__ ids, float* __restrict__ depth, float* __restrict__ var) {
-    __shared__ float smem[kSolveWarps * Geo<K>::WARP_FLOATS];
+    __shared__ __align__(16) float smem[kSolveWarps * Geo<K>::WARP_FLOATS];
     okrige_solve_block<K, true>(h, GridView{}, k, p, p0, nodes, ids, depth, var, blockIdx.x, smem,
                                 q.x, q.y);
 }

@@ -16,10 +16,11 @@
 // by its largest diagonal entry. It is assembled once per entry straight into
 // a 30-bit fixed-point copy in shared memory (packed lower triangle), factored
 // by Cholesky in FP32 with each thread's rows in registers (thread t, slot s
-// holds row G*s + t, columns 0 .. G*(s+1)-1; pivots and column entries move
-// between the G threads by warp shuffles). The back sweeps also run on the
-// register rows, one column at a time with a group sum (no transposed copy of
-// the factor), so shared memory per system stays near 2.5 KB (K = 32) and,
+// holds row G*s + t, columns 0 .. G*(s+1)-1; pivots move between the G
+// threads by warp shuffles, column entries through a small column buffer in
+// shared memory). The back sweeps also run on the register rows, one column at
+// a time with a group sum (no transposed copy of the factor), so shared
+// memory per system stays near 2.8 KB (K = 32) and,
 // with the registers held to 128, a GB300 SM keeps 16 warps resident. One
 // step of iterative refinement follows: x is rounded to 24-bit fixed point x'
 // (exact in FP32), the residual b - A' x' is accumulated exactly in 64-bit
@@ -54,9 +55,12 @@ struct Geo {
     static constexpr int TRI = K * (K + 1) / 2;           // packed lower triangle of A
     static constexpr int TAB = K + 1;                     // neighbour table length
     // per system: the fixed-point A as a packed lower triangle (row r at
-    // r (r + 1) / 2), then the three neighbour tables; the stride is = G
-    // (mod 32) so that the G-thread groups of a warp spread over the banks
-    static constexpr int RAW = TRI + 3 * TAB;
+    // r (r + 1) / 2), the three neighbour tables and two column buffers; the
+    // stride is = G (mod 32) so that the G-thread groups of a warp spread over
+    // the banks
+    // two column buffers for the Cholesky broadcasts (16-byte aligned)
+    static constexpr int CB = (TRI + 3 * TAB + 3) / 4 * 4;
+    static constexpr int RAW = CB + 2 * K;
     static constexpr int SYS_FLOATS = RAW + ((G - RAW % 32) + 32) % 32;
     static constexpr int WARP_FLOATS = SYS * SYS_FLOATS;
     static __host__ __device__ constexpr int off(int s) { return G * s * (s + 1) / 2; }
@@ -151,21 +155,27 @@ __device__ __forceinline__ void knn_ids_point_wide(const HashView& h, int qx, in
 
 __host__ __device__ constexpr int tri(int r) { return r * (r + 1) / 2; }
 
-// Cholesky column j of the register-held lower triangle: scale by the pivot,
-// then update the trailing rows with column j broadcast within the group.
+// Cholesky column j of the register-held lower triangle: scale by the pivot
+// (one shuffle), then update the trailing rows with column j. Each thread
+// publishes its four entries of the column with one 16-byte store to a
+// column buffer and reads the group's entries back four rows per 16-byte
+// load (broadcast): fewer instructions than one shuffle per row. Two buffers
+// alternate by column, so one __syncwarp per column orders writes and reads.
 // Expanded over j with an integer_sequence so every register index is a
 // compile-time constant (a nested #pragma unroll over the whole triangle is
 // beyond the unroller and would leave L in local memory).
 template <int K, int J>
 __device__ __forceinline__ void chol_column(float (&L)[Geo<K>::LEN], float (&dinv)[kR], int t,
-                                            int gbase) {
+                                            int gbase, float* cb) {
     using Gm = Geo<K>;
     constexpr int G = Gm::G;
     constexpr int SJ = J / G;
     const float d = __shfl_sync(kFull, L[Gm::off(SJ) + J], gbase + J % G);
     const float inv = rsqrtf(d);
+    float pub[kR];
 #pragma unroll
     for (int s = 0; s < kR; ++s) {
+        pub[s] = 0.0f;
         if (G * (s + 1) - 1 >= J) {
             const int r = G * s + t;
             if (r > J) L[Gm::off(s) + J] *= inv;
@@ -173,21 +183,48 @@ __device__ __forceinline__ void chol_column(float (&L)[Geo<K>::LEN], float (&din
                 L[Gm::off(s) + J] = d * inv;
                 dinv[s] = inv;
             }
+            pub[s] = L[Gm::off(s) + J];
         }
     }
+    if constexpr (G >= 4) {
+        // 16-byte aligned only when the per-system stride (= G mod 32) is a
+        // multiple of 4 floats
+        static_assert(kR == 4 && Gm::SYS_FLOATS % 4 == 0 && Gm::CB % 4 == 0, "float4 buffer");
+        float* col = cb + (J & 1) * K;
+        *reinterpret_cast<float4*>(col + 4 * t) = make_float4(pub[0], pub[1], pub[2], pub[3]);
+        __syncwarp();
 #pragma unroll
-    for (int c = J + 1; c < K; ++c) {
-        const float lcj = __shfl_sync(kFull, L[Gm::off(c / G) + J], gbase + c % G);
+        for (int tc = 0; tc < G; ++tc) {
+            if (G * (kR - 1) + tc <= J) continue;  // no row of this thread beyond J
+            const float4 q4 = *reinterpret_cast<const float4*>(col + 4 * tc);
+            const float q[4] = {q4.x, q4.y, q4.z, q4.w};
 #pragma unroll
-        for (int s = 0; s < kR; ++s)
-            if (G * (s + 1) - 1 >= c) L[Gm::off(s) + c] = fmaf(-L[Gm::off(s) + J], lcj, L[Gm::off(s) + c]);
+            for (int sc = 0; sc < kR; ++sc) {
+                const int c = G * sc + tc;
+                if (c <= J) continue;
+#pragma unroll
+                for (int s = 0; s < kR; ++s)
+                    if (G * (s + 1) - 1 >= c)
+                        L[Gm::off(s) + c] = fmaf(-L[Gm::off(s) + J], q[sc], L[Gm::off(s) + c]);
+            }
+        }
+    } else {
+        // small systems (G < 4): one shuffle per trailing row
+#pragma unroll
+        for (int c = J + 1; c < K; ++c) {
+            const float lcj = __shfl_sync(kFull, L[Gm::off(c / G) + J], gbase + c % G);
+#pragma unroll
+            for (int s = 0; s < kR; ++s)
+                if (G * (s + 1) - 1 >= c)
+                    L[Gm::off(s) + c] = fmaf(-L[Gm::off(s) + J], lcj, L[Gm::off(s) + c]);
+        }
     }
 }
 
 template <int K, int... J>
 __device__ __forceinline__ void chol_factor(float (&L)[Geo<K>::LEN], float (&dinv)[kR], int t,
-                                            int gbase, std::integer_sequence<int, J...>) {
-    (chol_column<K, J>(L, dinv, t, gbase), ...);
+                                            int gbase, float* cb, std::integer_sequence<int, J...>) {
+    (chol_column<K, J>(L, dinv, t, gbase, cb), ...);
 }
 
 // forward sweep step j of L y = v (L rows in registers)
@@ -322,19 +359,24 @@ __device__ __forceinline__ void okrige_solve_block(const HashView& h, const Grid
         const float sa = pow2f(ea), isa = pow2f(-ea);
         __syncwarp();
 
-        // assemble the lower triangle once per entry (the group's threads take
-        // the columns c = t, t + G, ... of each row), straight into fixed point
-        for (int r = 0; r < K; ++r) {
-            const bool row = r + 1 < ke;
-            const float xr = fx[r + 1], yr = fy[r + 1], grr = tg[r];
-            for (int c = t; c <= r; c += G) {
-                float v;
-                if (c == r)
-                    v = row ? 2.0f * grr : 1.0f;
-                else
-                    v = (row && c + 1 < ke)
-                            ? (grr + tg[c]) - gamma_pair_f(p, xr - fx[c + 1], yr - fy[c + 1])
-                            : 0.0f;
+        // assemble the lower triangle once per entry, straight into fixed
+        // point: thread t owns the columns c = t + G q; for each it walks the
+        // rows r >= G q in step with its group (rows above its column idle),
+        // so a row's entries land in consecutive banks and the unrolled walk
+        // gives the thread independent entries to overlap
+#pragma unroll
+        for (int q = 0; q < kR; ++q) {
+            const int c = t + G * q;
+            const float xc = fx[c + 1], yc = fy[c + 1], gcc = tg[c];
+            const float dg = (c + 1 < ke) ? 2.0f * gcc : 1.0f;
+#pragma unroll 4
+            for (int r = G * q; r < K; ++r) {
+                if (r < c) continue;
+                // a real row r (r + 1 < ke) implies a real column c < r
+                const float v = (r == c) ? dg
+                                : (r + 1 < ke)
+                                    ? (tg[r] + gcc) - gamma_pair_f(p, fx[r + 1] - xc, fy[r + 1] - yc)
+                                    : 0.0f;
                 Aq[tri(r) + c] = __float2int_rn(v * sa);
             }
         }
@@ -362,7 +404,7 @@ __device__ __forceinline__ void okrige_solve_block(const HashView& h, const Grid
         float dinv[kR];
 #pragma unroll
         for (int s = 0; s < kR; ++s) dinv[s] = 1.0f;
-        chol_factor<K>(L, dinv, t, gbase, std::make_integer_sequence<int, K>{});
+        chol_factor<K>(L, dinv, t, gbase, sysmem + Gm::CB, std::make_integer_sequence<int, K>{});
 
         // solve, one refinement step, solve again. The residual b - A' x' is
         // exact: x' is x rounded to 24-bit fixed point (representable in FP32),
@@ -394,17 +436,44 @@ __device__ __forceinline__ void okrige_solve_block(const HashView& h, const Grid
                 x[s] = (float)xq[s] * isx;
                 acc[s] = __float2ll_rn((b[s] * sa) * sx);
             }
-#pragma unroll
-            for (int sc = 0; sc < kR; ++sc) {
-#pragma unroll 4
+            if constexpr (G >= 4) {
+                // x' of the group through the column buffer: one 16-byte store
+                // per thread, four columns per 16-byte load
+                int* xb = reinterpret_cast<int*>(sysmem + Gm::CB);
+                *reinterpret_cast<int4*>(xb + 4 * t) = make_int4(xq[0], xq[1], xq[2], xq[3]);
+                __syncwarp();
+#pragma unroll 2
                 for (int tc = 0; tc < G; ++tc) {
-                    const int c = G * sc + tc;
-                    const int xc = __shfl_sync(kFull, xq[sc], gbase + tc);
+                    const int4 q4 = *reinterpret_cast<const int4*>(xb + 4 * tc);
+                    const int q[4] = {q4.x, q4.y, q4.z, q4.w};
 #pragma unroll
-                    for (int s = 0; s < kR; ++s) {
-                        const int r = G * s + t;
-                        const int a = Aq[tri(max(r, c)) + min(r, c)];
-                        acc[s] -= (long long)a * (long long)xc;
+                    for (int sc = 0; sc < kR; ++sc) {
+                        const int c = G * sc + tc;
+#pragma unroll
+                        for (int s = 0; s < kR; ++s) {
+                            // slots below / above mine hold columns below / above my row
+                            const int r = G * s + t;
+                            const int a = sc < s   ? Aq[tri(r) + c]
+                                          : sc > s ? Aq[tri(c) + r]
+                                                   : Aq[tri(max(r, c)) + min(r, c)];
+                            acc[s] -= (long long)a * (long long)q[sc];
+                        }
+                    }
+                }
+                __syncwarp();  // the buffer serves the next system's factor
+            } else {
+#pragma unroll
+                for (int sc = 0; sc < kR; ++sc) {
+#pragma unroll 4
+                    for (int tc = 0; tc < G; ++tc) {
+                        const int c = G * sc + tc;
+                        const int xc = __shfl_sync(kFull, xq[sc], gbase + tc);
+#pragma unroll
+                        for (int s = 0; s < kR; ++s) {
+                            const int r = G * s + t;
+                            const int a = Aq[tri(max(r, c)) + min(r, c)];
+                            acc[s] -= (long long)a * (long long)xc;
+                        }
                     }
                 }
             }

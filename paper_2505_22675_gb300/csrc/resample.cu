@@ -221,29 +221,41 @@ __global__ void __launch_bounds__(kThreads) k_resample_pts(Src s, const int32_t*
     }
 }
 
-// output grid: block b takes row b / chunks and kThreads * kPer columns of
-// it; the row's position along y and its source rows are the block's
+// output grid: block b takes kThreads * kPer columns (chunk b % chunks) of
+// kRowsPerBlock consecutive rows; a thread's four column positions in the
+// source lattice (one integer division each) serve all its rows
+constexpr int kRowsPerBlock = 8;
+
 template <int kMethod>
-__global__ void __launch_bounds__(kThreads) k_resample_grid(Src s, GridView o, int chunks,
+__global__ void __launch_bounds__(kThreads, kMethod == BG_RESAMPLE_CATMULL_ROM ? 4 : 1)
+    k_resample_grid(Src s, GridView o, int chunks,
                                                             float* __restrict__ out,
                                                             int8_t* __restrict__ how_out) {
-    const int row = blockIdx.x / chunks;
-    const int c0 = (blockIdx.x - row * chunks) * kThreads * kPer + threadIdx.x;
-    const Axis ay = axis_of((int64_t)o.y0 + (int64_t)row * o.cell + o.cell / 2 - s.cy0, s.cell, s.ny);
-    const float* rows[4];
-    row_ptrs(s, ay.i, rows);
+    const int band = blockIdx.x / chunks;
+    const int c0 = (blockIdx.x - band * chunks) * kThreads * kPer + threadIdx.x;
     const int64_t ux0 = (int64_t)o.x0 + o.cell / 2 - s.cx0;
+    Axis ax[kPer];
 #pragma unroll
     for (int k = 0; k < kPer; ++k) {
         const int c = c0 + k * kThreads;
-        const int cc = c < o.nx ? c : o.nx - 1;
-        const Axis ax = axis_of(ux0 + (int64_t)cc * o.cell, s.cell, s.nx);
-        int8_t how;
-        const float f = resample_at<kMethod>(s, ax, ay, rows, how);
-        if (c < o.nx) {
-            const int64_t p = (int64_t)row * o.nx + c;
-            out[p] = f;
-            if (how_out) how_out[p] = how;
+        ax[k] = axis_of(ux0 + (int64_t)(c < o.nx ? c : o.nx - 1) * o.cell, s.cell, s.nx);
+    }
+    const int row1 = min(o.ny, (band + 1) * kRowsPerBlock);
+    for (int row = band * kRowsPerBlock; row < row1; ++row) {
+        const Axis ay =
+            axis_of((int64_t)o.y0 + (int64_t)row * o.cell + o.cell / 2 - s.cy0, s.cell, s.ny);
+        const float* rows[4];
+        row_ptrs(s, ay.i, rows);
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            const int c = c0 + k * kThreads;
+            int8_t how;
+            const float f = resample_at<kMethod>(s, ax[k], ay, rows, how);
+            if (c < o.nx) {
+                const int64_t p = (int64_t)row * o.nx + c;
+                out[p] = f;
+                if (how_out) how_out[p] = how;
+            }
         }
     }
 }
@@ -272,7 +284,7 @@ bg_status launch_resample_grid(const float* src, const GridView& g, int method, 
                                float* out, int8_t* how, cudaStream_t st) {
     const Src s{src, g.x0 + g.cell / 2, g.y0 + g.cell / 2, g.cell, g.nx, g.ny, 1.0f / (float)g.cell};
     const int chunks = (o.nx + kThreads * kPer - 1) / (kThreads * kPer);
-    const int64_t blocks = (int64_t)chunks * o.ny;
+    const int64_t blocks = (int64_t)chunks * ((o.ny + kRowsPerBlock - 1) / kRowsPerBlock);
     if (blocks >= ((int64_t)1 << 31)) {
         set_error("output grid too large for one launch");
         return BG_ERR_INVALID_ARG;
