@@ -48,7 +48,17 @@ def swath_run():
     out["ok"] = (d[sel_t].cpu().numpy(), v[sel_t].cpu().numpy(),
                  nb.view(g.m, 32)[sel_t].cpu().numpy(), int(torch.isnan(d).sum()),
                  float(v.min()))
-    del d, v, nb
+    del nb
+    # without nbr_out the grid runs in row chunks of about 1 GiB of ids (nine
+    # here) instead of one pass over all ids; every node must come out
+    # bitwise the same
+    d2 = torch.empty(g.m, device=dev)
+    v2 = torch.empty(g.m, device=dev)
+    bg.interp_okrige(s, grid, 32, bg.variogram(0, 0.25, 100.0, 50.0), d2, v2)
+    torch.cuda.synchronize()
+    out["ok_same_without_nbr"] = bool(torch.equal(d.view(torch.int32), d2.view(torch.int32))
+                                      and torch.equal(v.view(torch.int32), v2.view(torch.int32)))
+    del d, v, d2, v2
     torch.cuda.synchronize()
     bg.soundings_destroy(s)
     bg.grid_destroy(grid)
@@ -75,3 +85,7 @@ def test_swath_okrige_k32(swath_run):
                                  want_idx=True)
     assert np.array_equal(nb, ridx)
     assert_okrige(d, v, rd, rv, 0.25)
+
+
+def test_swath_okrige_row_chunks_match_one_pass(swath_run):
+    assert swath_run[3]["ok_same_without_nbr"]
