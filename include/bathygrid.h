@@ -153,6 +153,20 @@ bg_status bg_interp_okrige(bg_soundings_t s, bg_grid_t grid, int k, const bg_var
                            float* depth_out, float* var_out, int32_t* nbr_out,
                            void* cuda_stream);
 
+/* IDW and ordinary kriging of the same grid in one pass: one exact k-NN search
+ * of k_okrige neighbours per node feeds both, and the IDW takes the first
+ * k_idw of them (the k_idw nearest, in the same (d2, index) order). Every
+ * output is bitwise what bg_interp_idw and bg_interp_okrige give when called
+ * one after the other; the k-NN search is not repeated. The paper runs its
+ * methods separately; this entry point is for callers that want both grids.
+ *   k_idw in [1, k_okrige], k_okrige in [1, 32]; power > 0; v as for
+ *   bg_interp_okrige.
+ *   idw_out, depth_out: device, nx*ny float32 each; var_out: device or NULL.
+ * Asynchronous on cuda_stream. */
+bg_status bg_interp_idw_okrige(bg_soundings_t s, bg_grid_t grid, int k_idw, float power,
+                               int k_okrige, const bg_variogram* v, float* idw_out,
+                               float* depth_out, float* var_out, void* cuda_stream);
+
 /* The same two methods at a list of query points instead of grid nodes: the
  * paper's hole filling interpolates the missing entries of a grid (Sec. IV,
  * Grid B) and its runtime tests interpolate batches of generated points

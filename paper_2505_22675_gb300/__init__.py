@@ -28,7 +28,7 @@ __all__ = [
     "version", "launch_count", "profile_enable", "profile_read", "ctx_create", "ctx_destroy",
     "ctx_device_bytes", "grid_create", "grid_destroy",
     "soundings_upload", "soundings_info", "soundings_destroy", "interp_idw", "interp_okrige",
-    "interp_idw_points", "interp_okrige_points", "BILINEAR", "CATMULL_ROM", "resample_points",
+    "interp_idw_okrige", "interp_idw_points", "interp_okrige_points", "BILINEAR", "CATMULL_ROM", "resample_points",
     "resample_grid",
     "variogram", "interp_idw_noalloc", "submit", "poll", "wait", "cancel", "serve_stats",
     "serve_shutdown", "Request", "Result", "Batch", "batch_create", "batch_run", "batch_tune",
@@ -179,6 +179,19 @@ def interp_okrige(s, grid, k: int, vgm: Variogram, depth_out, var_out=None, nbr_
         _check_dtype(nbr_out, "int32")
     check(_lib().bg_interp_okrige(s, grid, k, ctypes.byref(vgm), _ptr(depth_out), _ptr(var_out),
                                   _ptr(nbr_out), _stream(stream, depth_out)), "bg_interp_okrige")
+
+
+def interp_idw_okrige(s, grid, k_idw: int, power: float, k_okrige: int, vgm: Variogram, idw_out,
+                      depth_out, var_out=None, stream=None) -> None:
+    """IDW (first k_idw neighbours) and ordinary kriging (k_okrige) in one pass;
+    bitwise the results of interp_idw and interp_okrige called separately."""
+    for t in (idw_out, depth_out):
+        _check_dtype(t, "float32")
+    if var_out is not None:
+        _check_dtype(var_out, "float32")
+    check(_lib().bg_interp_idw_okrige(s, grid, k_idw, power, k_okrige, ctypes.byref(vgm),
+                                      _ptr(idw_out), _ptr(depth_out), _ptr(var_out),
+                                      _stream(stream, depth_out)), "bg_interp_idw_okrige")
 
 
 def _check_points(qx_cm, qy_cm, depth_out):

@@ -57,9 +57,9 @@ constexpr int kBT = 256;          // threads of those kernels
 constexpr int kItemThreads = 128;
 constexpr int kBatchSolveBlocks = 8;  // solve blocks per claimed item: one atomic per 64 systems
 // The persistent solve reads its tile descriptor from shared memory, which
-// raises its register needs: it runs faster with 6 resident blocks (no
+// raises its register needs: it runs faster with 12 resident warps (no
 // spills) than held to the per-grid kernel's 128 registers.
-constexpr int kBatchSolveBlocksPerSM = 6;
+constexpr int kBatchSolveBlocksPerSM = 12 / kSolveWarps;
 
 __device__ __forceinline__ int upper_tile(const int64_t* off, int T, int64_t v) {
     // largest t with off[t] <= v  (off ascending, off[0] = 0)

@@ -50,6 +50,14 @@ struct GridView {
     int32_t x0, y0, cell, nx, ny;
 };
 
+// IDW fused into a kriging pass: depth over the first k of the kriging's
+// sorted neighbours, weights d^-power (out == nullptr: none).
+struct IdwFuse {
+    float* out = nullptr;
+    float power = 2.0f;
+    int k = 0;
+};
+
 // Query points: m device coordinates (cm) in two arrays.
 struct PointsView {
     const int32_t* x;
@@ -190,8 +198,10 @@ bg_status launch_idw_with_flag(const bg_soundings_s* s, const GridView& g, int k
 // pass whether the packed pass left nodes for it.
 bg_status launch_idw(const bg_soundings_s* s, const GridView& g, int k, float power,
                      float* depth, int32_t* nbr, cudaStream_t st);
+// fz: NULL, or an IDW to write in the same pass (fz->k <= k)
 bg_status launch_okrige(const bg_soundings_s* s, const GridView& g, int k, const OkParams& p,
-                        float* depth, float* var, int32_t* nbr, cudaStream_t st);
+                        float* depth, float* var, int32_t* nbr, cudaStream_t st,
+                        const IdwFuse* fz = nullptr);
 
 // Gridded input (bilinear / Catmull-Rom) at query points or output-grid nodes;
 // no allocation.

@@ -341,31 +341,6 @@ bg_status bg_interp_idw(bg_soundings_t s, bg_grid_t grid, int k, float power, fl
     return launch_idw(s, grid->g, k, power, depth_out, nbr_out, (cudaStream_t)cuda_stream);
 }
 
-bg_status bg_interp_okrige(bg_soundings_t s, bg_grid_t grid, int k, const bg_variogram* v,
-                           float* depth_out, float* var_out, int32_t* nbr_out, void* cuda_stream) {
-    bg_status rc = check_interp(s, grid, k, depth_out);
-    if (rc != BG_OK) return rc;
-    BG_REQUIRE(v, "variogram is NULL");
-    BG_REQUIRE(v->model == BG_VARIOGRAM_SPHERICAL || v->model == BG_VARIOGRAM_EXPONENTIAL,
-               "unknown variogram model");
-    BG_REQUIRE(std::isfinite(v->nugget_m2) && v->nugget_m2 >= 0.0f, "nugget must be >= 0");
-    BG_REQUIRE(std::isfinite(v->sill_m2) && v->sill_m2 > v->nugget_m2, "sill must exceed the nugget");
-    BG_REQUIRE(finite_pos(v->range_m), "range must be > 0");
-    DeviceGuard dg(s->ctx->device);
-    if (!dg.ok) return cuda_fail(cudaGetLastError(), "cudaSetDevice");
-    OkParams p{v->model, v->nugget_m2, v->sill_m2 - v->nugget_m2, v->sill_m2, 1.0f / v->range_m};
-    return launch_okrige(s, grid->g, k, p, depth_out, var_out, nbr_out, (cudaStream_t)cuda_stream);
-}
-
-static bg_status check_points(bg_soundings_t s, const int32_t* qx, const int32_t* qy, int64_t m,
-                              int k, float* depth) {
-    BG_REQUIRE(s, "NULL handle");
-    BG_REQUIRE(m >= 0 && m < ((int64_t)1 << 40), "m must be in [0, 2^40)");
-    BG_REQUIRE(m == 0 || (qx && qy && depth), "NULL query or output pointer");
-    BG_REQUIRE(k >= 1 && k <= 32, "k must be in [1, 32]");
-    return BG_OK;
-}
-
 static bool okrige_params(const bg_variogram* v, OkParams* p) {
     if (!v) return set_error("variogram is NULL"), false;
     if (v->model != BG_VARIOGRAM_SPHERICAL && v->model != BG_VARIOGRAM_EXPONENTIAL)
@@ -378,6 +353,48 @@ static bool okrige_params(const bg_variogram* v, OkParams* p) {
     *p = OkParams{v->model, v->nugget_m2, v->sill_m2 - v->nugget_m2, v->sill_m2, 1.0f / v->range_m};
     return true;
 }
+
+bg_status bg_interp_okrige(bg_soundings_t s, bg_grid_t grid, int k, const bg_variogram* v,
+                           float* depth_out, float* var_out, int32_t* nbr_out, void* cuda_stream) {
+    bg_status rc = check_interp(s, grid, k, depth_out);
+    if (rc != BG_OK) return rc;
+    OkParams p;
+    if (!okrige_params(v, &p)) return BG_ERR_INVALID_ARG;
+    DeviceGuard dg(s->ctx->device);
+    if (!dg.ok) return cuda_fail(cudaGetLastError(), "cudaSetDevice");
+    return launch_okrige(s, grid->g, k, p, depth_out, var_out, nbr_out, (cudaStream_t)cuda_stream);
+}
+
+
+bg_status bg_interp_idw_okrige(bg_soundings_t s, bg_grid_t grid, int k_idw, float power,
+                               int k_okrige, const bg_variogram* v, float* idw_out,
+                               float* depth_out, float* var_out, void* cuda_stream) {
+    bg_status rc = check_interp(s, grid, k_okrige, depth_out);
+    if (rc != BG_OK) return rc;
+    BG_REQUIRE(idw_out, "idw_out is NULL");
+    BG_REQUIRE(k_idw >= 1 && k_idw <= k_okrige, "k_idw must be in [1, k_okrige]");
+    BG_REQUIRE(finite_pos(power), "power must be finite and > 0");
+    OkParams p;
+    if (!okrige_params(v, &p)) return BG_ERR_INVALID_ARG;
+    DeviceGuard dg(s->ctx->device);
+    if (!dg.ok) return cuda_fail(cudaGetLastError(), "cudaSetDevice");
+    IdwFuse fz;
+    fz.out = idw_out;
+    fz.power = power;
+    fz.k = k_idw;
+    return launch_okrige(s, grid->g, k_okrige, p, depth_out, var_out, nullptr,
+                         (cudaStream_t)cuda_stream, &fz);
+}
+
+static bg_status check_points(bg_soundings_t s, const int32_t* qx, const int32_t* qy, int64_t m,
+                              int k, float* depth) {
+    BG_REQUIRE(s, "NULL handle");
+    BG_REQUIRE(m >= 0 && m < ((int64_t)1 << 40), "m must be in [0, 2^40)");
+    BG_REQUIRE(m == 0 || (qx && qy && depth), "NULL query or output pointer");
+    BG_REQUIRE(k >= 1 && k <= 32, "k must be in [1, 32]");
+    return BG_OK;
+}
+
 
 bg_status bg_interp_idw_points(bg_soundings_t s, const int32_t* qx_cm, const int32_t* qy_cm,
                                int64_t m, int k, float power, float* depth_out, int32_t* nbr_out,

@@ -7,9 +7,10 @@
 // soundings. It is evaluated as z_1 + sum w_i (z_i - z_1) / sum w_i with
 // z_1 the nearest sounding's depth and w_i = (d_1^2 / d_i^2)^(p/2): the same
 // quantity, but every term is an anomaly of a few metres (so only the final
-// add rounds at ~3500 m) and every weight is in (0, 1]. Accumulation follows
-// the ascending (d2, index) order, so a node's result does not depend on the
-// cell size, the launch shape or what else runs.
+// add rounds at ~3500 m) and every weight is in (0, 1]. The sums run in one
+// fixed order over the ascending (d2, index) list (idw_tree8), so a node's
+// result does not depend on the cell size, the launch shape, the kernel or
+// what else runs.
 
 
 #pragma once
@@ -22,6 +23,30 @@
 namespace bg {
 
 
+// d2 as float: a 32-bit conversion when it fits (64-bit ones use the FP64 pipe)
+__device__ __forceinline__ float idw_d2f(uint64_t v) {
+    return v < (1ull << 31) ? __int2float_rn((int)v) : __ull2float_rn(v);
+}
+
+// weight of a neighbour at squared distance di relative to the nearest (d1):
+// (d1 / di)^(p/2), with l1 = log2(d1) and hp = p / 2
+__device__ __forceinline__ float idw_weight(float d1, float l1, float hp, float power, float di) {
+    return (power == 2.0f) ? d1 / di : exp2f(hp * (l1 - log2f(di)));
+}
+
+// The sums of an IDW run in one fixed order, so that every kernel that forms
+// them gets bitwise the same depth: neighbour n >= 1 goes to partial n_t =
+// (n - 1) mod 8, each partial adds its neighbours in ascending n, and the 8
+// partials combine pairwise as ((p0 + p1) + (p2 + p3)) + ((p4 + p5) + (p6 +
+// p7)). The kriging solve (8 threads per system, thread t holding neighbours
+// 1 + t + 8 s) forms the same partials in registers and combines them with
+// xor shuffles in that pattern.
+constexpr int kIdwLanes = 8;
+
+__device__ __forceinline__ float idw_tree8(const float (&p)[kIdwLanes]) {
+    return ((p[0] + p[1]) + (p[2] + p[3])) + ((p[4] + p[5]) + (p[6] + p[7]));
+}
+
 // IDW from the neighbours in ascending (d2, index) order; get(i) returns
 // (d2, upload index) of the i-th.
 template <class Get>
@@ -33,25 +58,25 @@ __device__ __forceinline__ float idw_from(const HashView& h, int keff, float pow
     get(0, d0, i0);
     const float z1 = __int_as_float(__ldg(zb + 4 * (int64_t)i0));
     if (d0 == 0) return z1;  // node on top of a sounding
-    // d2 as float: a 32-bit conversion when it fits (64-bit ones use the FP64 pipe)
-    auto d2f = [](uint64_t v) {
-        return v < (1ull << 31) ? __int2float_rn((int)v) : __ull2float_rn(v);
-    };
-    const float d1 = d2f(d0);
+    const float d1 = idw_d2f(d0);
     const float l1 = log2f(d1);
     const float hp = 0.5f * power;
-    float num = 0.0f, den = 1.0f;  // i = 0 contributes w = 1, anomaly 0
-    for (int i = 1; i < keff; ++i) {
+    float num[kIdwLanes], den[kIdwLanes];
+#pragma unroll
+    for (int q = 0; q < kIdwLanes; ++q) num[q] = den[q] = 0.0f;
+#pragma unroll
+    for (int n = 1; n < 32; ++n) {
+        if (n >= keff) break;
         uint64_t di2;
         int ii;
-        get(i, di2, ii);
+        get(n, di2, ii);
         const float zi = __int_as_float(__ldg(zb + 4 * (int64_t)ii));
-        const float di = d2f(di2);
-        const float w = (power == 2.0f) ? d1 / di : exp2f(hp * (l1 - log2f(di)));
-        num = fmaf(w, zi - z1, num);
-        den += w;
+        const float w = idw_weight(d1, l1, hp, power, idw_d2f(di2));
+        num[(n - 1) % kIdwLanes] = fmaf(w, zi - z1, num[(n - 1) % kIdwLanes]);
+        den[(n - 1) % kIdwLanes] += w;
     }
-    return z1 + num / den;
+    // neighbour 0 contributes weight 1 and anomaly 0
+    return z1 + idw_tree8(num) / (1.0f + idw_tree8(den));
 }
 
 template <int K, bool kWide>

@@ -45,17 +45,19 @@ __global__ void __launch_bounds__(128) k_knn_ids_wide(HashView h, GridView g, in
                               nullptr);
 }
 
-template <int K>
+template <int K, bool kIdw>
 __global__ void __launch_bounds__(kSolveWarps * 32, kSolveBlocksPerSM) k_okrige_solve(
     HashView h, GridView g, int k, OkParams p, int64_t node0, int64_t nodes,
-    const int32_t* __restrict__ ids, float* __restrict__ depth, float* __restrict__ var) {
+    const int32_t* __restrict__ ids, float* __restrict__ depth, float* __restrict__ var,
+    IdwFuse fz) {
     __shared__ __align__(16) float smem[kSolveWarps * Geo<K>::WARP_FLOATS];
-    okrige_solve_block<K>(h, g, k, p, node0, nodes, ids, depth, var, blockIdx.x, smem);
+    okrige_solve_block<K, false, kIdw>(h, g, k, p, node0, nodes, ids, depth, var, blockIdx.x, smem,
+                                       nullptr, nullptr, fz);
 }
 
 template <int K>
 bg_status launch_k(const HashView& h, const GridView& g, int k, const OkParams& p, float* depth,
-                   float* var, int32_t* nbr, bg_ctx_s* ctx, cudaStream_t st) {
+                   float* var, int32_t* nbr, bg_ctx_s* ctx, cudaStream_t st, const IdwFuse* fz) {
     using Gm = Geo<K>;
     // grid rows per chunk: the id buffer stays near 1 GiB unless the caller
     // passed nbr_out, which then holds all ids
@@ -90,8 +92,17 @@ bg_status launch_k(const HashView& h, const GridView& g, int k, const OkParams& 
         const int64_t sb = (nodes + sys_per_block - 1) / sys_per_block;
         {
             ProfScope ps(ctx, kProfSolve, nodes, st);
-            k_okrige_solve<K><<<(unsigned)sb, kSolveWarps * 32, 0, st>>>(h, g, k, p, j0 * g.nx, nodes,
-                                                                         chunk_ids, depth, var);
+            bool fused = false;
+            if constexpr (K == 32) {  // the fused IDW runs with 8 threads per system
+                if (fz) {
+                    k_okrige_solve<K, true><<<(unsigned)sb, kSolveWarps * 32, 0, st>>>(
+                        h, g, k, p, j0 * g.nx, nodes, chunk_ids, depth, var, *fz);
+                    fused = true;
+                }
+            }
+            if (!fused)
+                k_okrige_solve<K, false><<<(unsigned)sb, kSolveWarps * 32, 0, st>>>(
+                    h, g, k, p, j0 * g.nx, nodes, chunk_ids, depth, var, IdwFuse{});
         }
         note_launches(3);
         e = cudaGetLastError();
@@ -213,15 +224,23 @@ bg_status launch_okrige_points(const bg_soundings_s* s, const PointsView& q, int
 }
 
 bg_status launch_okrige(const bg_soundings_s* s, const GridView& g, int k, const OkParams& p,
-                        float* depth, float* var, int32_t* nbr, cudaStream_t st) {
+                        float* depth, float* var, int32_t* nbr, cudaStream_t st,
+                        const IdwFuse* fz) {
     HashView h = s->h;
     const int K = k <= 4 ? 4 : k <= 8 ? 8 : k <= 16 ? 16 : 32;
+    if (fz && K != 32) {
+        // smaller systems run 2 or 4 threads each: the IDW takes its own pass
+        // (the same depths: idw_from sums in the same fixed order)
+        const bg_status rc = launch_idw(s, g, fz->k, fz->power, fz->out, nullptr, st);
+        if (rc != BG_OK) return rc;
+        fz = nullptr;
+    }
     h.r0 = start_halfwidth(s, K);
     switch (K) {
-        case 4: return launch_k<4>(h, g, k, p, depth, var, nbr, s->ctx, st);
-        case 8: return launch_k<8>(h, g, k, p, depth, var, nbr, s->ctx, st);
-        case 16: return launch_k<16>(h, g, k, p, depth, var, nbr, s->ctx, st);
-        default: return launch_k<32>(h, g, k, p, depth, var, nbr, s->ctx, st);
+        case 4: return launch_k<4>(h, g, k, p, depth, var, nbr, s->ctx, st, fz);
+        case 8: return launch_k<8>(h, g, k, p, depth, var, nbr, s->ctx, st, fz);
+        case 16: return launch_k<16>(h, g, k, p, depth, var, nbr, s->ctx, st, fz);
+        default: return launch_k<32>(h, g, k, p, depth, var, nbr, s->ctx, st, fz);
     }
 }
 

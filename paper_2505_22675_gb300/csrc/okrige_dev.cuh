@@ -37,15 +37,16 @@
 #include <utility>
 
 #include "bg_internal.h"
+#include "idw_dev.cuh"
 #include "knn.cuh"
 
 namespace bg {
 
 
 constexpr int kR = 4;            // rows per thread
-constexpr int kSolveWarps = 2;   // warps per solve block
+constexpr int kSolveWarps = 4;   // warps per solve block
 constexpr int kRounds = 1;       // system batches per warp (one: more, shorter blocks balance best)
-constexpr int kSolveBlocksPerSM = 8;  // launch bound: 16 warps resident (128 registers)
+constexpr int kSolveBlocksPerSM = 4;  // launch bound: 16 warps resident (128 registers)
 
 template <int K>
 struct Geo {
@@ -72,7 +73,9 @@ __device__ __forceinline__ float variogram(const OkParams& p, float h_m) {
         if (t >= 1.0f) return p.sill;
         return fmaf(p.c * t, fmaf(-0.5f * t, t, 1.5f), p.c0);
     }
-    return fmaf(p.c, 1.0f - __expf(-h_m * p.inv_a), p.c0);
+    // 1 - exp(-t) as -expm1(-t): no cancellation at short range, where the
+    // model without a nugget makes the kriging variance small
+    return fmaf(p.c, -expm1f(-h_m * p.inv_a), p.c0);
 }
 
 // gamma from a separation in cm; zero separation gives `at_zero`
@@ -94,7 +97,7 @@ __device__ __forceinline__ float gamma_pair_f(const OkParams& p, float dx, float
         const float t = fminf(h_cm * p.inv_a * 0.01f, 1.0f);
         return fmaf(p.c * t, fmaf(-0.5f * t, t, 1.5f), p.c0);
     }
-    return fmaf(p.c, 1.0f - __expf(-h_cm * p.inv_a * 0.01f), p.c0);
+    return fmaf(p.c, -expm1f(-h_cm * p.inv_a * 0.01f), p.c0);
 }
 
 // ------------------------------------------------------------ k-NN -> ids
@@ -281,7 +284,10 @@ __device__ __forceinline__ int exp_above(float v) { return ((__float_as_int(v) >
 // neighbour ids of node node0 + i at ids[i * k]. smem: kSolveWarps * WARP_FLOATS.
 // With kPts the "nodes" are query points whose coordinates are px[], py[]
 // (g unused).
-template <int K, bool kPts = false>
+// With kIdw the block also writes the IDW depth over the first fz.k of the
+// node's sorted neighbours (fz.k <= k): the same value bg_interp_idw gives, as
+// its operations are those of idw_from in the same order.
+template <int K, bool kPts = false, bool kIdw = false>
 __device__ __forceinline__ void okrige_solve_block(const HashView& h, const GridView& g, int k,
                                                    const OkParams& p, int64_t node0, int64_t nodes,
                                                    const int32_t* __restrict__ ids,
@@ -289,7 +295,8 @@ __device__ __forceinline__ void okrige_solve_block(const HashView& h, const Grid
                                                    float* __restrict__ var, int64_t blk,
                                                    float* smem,
                                                    const int32_t* __restrict__ px = nullptr,
-                                                   const int32_t* __restrict__ py = nullptr) {
+                                                   const int32_t* __restrict__ py = nullptr,
+                                                   IdwFuse fz = IdwFuse{}) {
     using Gm = Geo<K>;
     constexpr int G = Gm::G;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -336,12 +343,30 @@ __device__ __forceinline__ void okrige_solve_block(const HashView& h, const Grid
         const float g00 = gamma_cm(p, r0.x - qx, r0.y - qy, 0.0f);
         float zr[kR], gr0[kR], g0r[kR];  // depth; Gamma(row's neighbour, nbr 0); gamma(node, row's nbr)
         float gmax = 0.0f;
+        // fused IDW: squared distance to the nearest, and each row's weight and anomaly
+        uint64_t idw_d0 = 0;
+        float idw_d1 = 0.0f, idw_l1 = 0.0f, idw_w[kR], idw_a[kR];
+        if constexpr (kIdw) {
+            const long long dx = (long long)r0.x - qx, dy = (long long)r0.y - qy;
+            idw_d0 = (uint64_t)(dx * dx + dy * dy);
+            idw_d1 = idw_d2f(idw_d0);
+            idw_l1 = log2f(idw_d1);
+        }
 #pragma unroll
         for (int s = 0; s < kR; ++s) {
             int4 rr = make_int4(0, 0, 0, 0);
             const bool real = nid[s] >= 0;
             if (real) rr = __ldg(h.orig + nid[s]);
             const int r = G * s + t;
+            if constexpr (kIdw) {
+                idw_w[s] = idw_a[s] = 0.0f;
+                if (G * s + 1 < fz.k) {  // uniform: this slot holds IDW neighbours
+                    const long long dx = (long long)rr.x - qx, dy = (long long)rr.y - qy;
+                    idw_w[s] = idw_weight(idw_d1, idw_l1, 0.5f * fz.power, fz.power,
+                                          idw_d2f((uint64_t)(dx * dx + dy * dy)));
+                    idw_a[s] = __int_as_float(rr.z) - z0;
+                }
+            }
             const float ox = (float)(rr.x - r0.x), oy = (float)(rr.y - r0.y);
             fx[r + 1] = ox;
             fy[r + 1] = oy;
@@ -353,6 +378,27 @@ __device__ __forceinline__ void okrige_solve_block(const HashView& h, const Grid
         }
 #pragma unroll
         for (int o = 1; o < G; o <<= 1) gmax = fmaxf(gmax, __shfl_xor_sync(kFull, gmax, o));
+        if constexpr (kIdw) {
+            // thread t's partial holds neighbours 1 + t + G s in ascending s,
+            // and the xor shuffles combine the partials as idw_tree8 does
+            static_assert(G == kIdwLanes, "the fused IDW runs with 8 threads per system");
+            const int ki = min(fz.k, ke);
+            float num = 0.0f, den = 0.0f;
+#pragma unroll
+            for (int s = 0; s < kR; ++s)
+                if (1 + G * s + t < ki) {
+                    num = fmaf(idw_w[s], idw_a[s], num);
+                    den += idw_w[s];
+                }
+#pragma unroll
+            for (int o = 1; o < G; o <<= 1) {
+                num += __shfl_xor_sync(kFull, num, o);
+                den += __shfl_xor_sync(kFull, den, o);
+            }
+            if (live && t == 0)
+                fz.out[node] = ke == 0 ? __int_as_float(0x7fc00000)
+                                       : (idw_d0 == 0 ? z0 : z0 + num / (1.0f + den));
+        }
         // A is SPD, so |A[r][c]| <= its largest diagonal entry max(1, 2 max Gamma_r0);
         // fixed point with 30 bits below that bound
         const int ea = 30 - exp_above(fmaxf(1.0f, 2.0f * gmax));

@@ -58,7 +58,16 @@ def swath_run():
     torch.cuda.synchronize()
     out["ok_same_without_nbr"] = bool(torch.equal(d.view(torch.int32), d2.view(torch.int32))
                                       and torch.equal(v.view(torch.int32), v2.view(torch.int32)))
-    del d, v, d2, v2
+    # the fused pass (one k-NN for both methods) gives bitwise the same grids
+    fi, fd, fv = (torch.empty(g.m, device=dev) for _ in range(3))
+    bg.interp_idw_okrige(s, grid, 16, 2.0, 32, bg.variogram(0, 0.25, 100.0, 50.0), fi, fd, fv)
+    di = torch.empty(g.m, device=dev)
+    bg.interp_idw(s, grid, 16, 2.0, di)
+    torch.cuda.synchronize()
+    out["fused_same"] = bool(torch.equal(fi.view(torch.int32), di.view(torch.int32))
+                             and torch.equal(fd.view(torch.int32), d.view(torch.int32))
+                             and torch.equal(fv.view(torch.int32), v.view(torch.int32)))
+    del d, v, d2, v2, fi, fd, fv, di
     torch.cuda.synchronize()
     bg.soundings_destroy(s)
     bg.grid_destroy(grid)
@@ -89,3 +98,7 @@ def test_swath_okrige_k32(swath_run):
 
 def test_swath_okrige_row_chunks_match_one_pass(swath_run):
     assert swath_run[3]["ok_same_without_nbr"]
+
+
+def test_swath_fused_pass_matches_separate_calls(swath_run):
+    assert swath_run[3]["fused_same"]
