@@ -61,11 +61,11 @@ def okrige_fp64_flops_per_node(k=OK_K):
     return 2 * n * n
 
 
-# DRAM bytes (read + write) per node of k_okrige_solve<32>, from one ncu
-# capture of the current kernel on the 2-line swath (3.384M nodes: 451.7 MB
-# read + 26.3 MB written per launch, mostly the 128 B of neighbour ids per
-# node); traffic grows with the nodes of a launch.
-SOLVE_DRAM_BYTES_PER_NODE = (451.745024e6 + 26.281728e6) / 3.384e6
+# DRAM bytes (read + write) per node of k_okrige_solve<32> with the fused IDW,
+# from one ncu capture of the current kernel on the 2-line swath (3.384M
+# nodes: 450.4 MB read + 38.3 MB written per launch, mostly the 128 B of
+# neighbour ids per node); traffic grows with the nodes of a launch.
+SOLVE_DRAM_BYTES_PER_NODE = (450.415104e6 + 38.339328e6) / 3.384e6
 
 # FP32 peak for "alu"-bound roofline: 152 SMs x 128 FP32 lanes x 2 flops/FMA x
 # the maximum SM clock (2,070 MHz) = 80.5 TFLOP/s.

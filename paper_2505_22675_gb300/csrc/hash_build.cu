@@ -364,9 +364,10 @@ bg_status build_soundings(bg_ctx_s* ctx, const int32_t* x, const int32_t* y, con
     const int64_t W = (int64_t)a[2] - a[0] + 1, H = (int64_t)a[3] - a[1] + 1;
     int64_t cs = cell_hint;
     if (cs <= 0) {
-        // about two soundings per cell at the mean density of the bounding box
+        // about four soundings per cell at the mean density of the bounding box
+        // (measured on the swath: 2 or 8 per cell make the k-NN 3-6% slower)
         const double rho = (double)nvalid / ((double)W * (double)H);
-        cs = (int64_t)std::ceil(std::sqrt(2.0 / rho));
+        cs = (int64_t)std::ceil(std::sqrt(4.0 / rho));
     }
     if (cs < 1) cs = 1;
     if (cs > kCoordLimit) cs = kCoordLimit;
@@ -485,7 +486,7 @@ bg_status build_hash_in_arena(const int32_t* x, const int32_t* y, const float* z
 
     const int64_t W = (int64_t)a[2] - a[0] + 1, H = (int64_t)a[3] - a[1] + 1;
     const double rho = (double)nvalid / ((double)W * (double)H);
-    int64_t cs = (int64_t)std::ceil(std::sqrt(2.0 / rho));
+    int64_t cs = (int64_t)std::ceil(std::sqrt(4.0 / rho));
     if (cs < 1) cs = 1;
     if (cs > kCoordLimit) cs = kCoordLimit;
     int64_t ncx = 0, ncy = 0, nb = 0, nch = 0, sat_rows = kSatRows;

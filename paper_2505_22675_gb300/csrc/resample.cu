@@ -227,7 +227,7 @@ __global__ void __launch_bounds__(kThreads) k_resample_pts(Src s, const int32_t*
 constexpr int kRowsPerBlock = 8;
 
 template <int kMethod>
-__global__ void __launch_bounds__(kThreads, kMethod == BG_RESAMPLE_CATMULL_ROM ? 4 : 1)
+__global__ void __launch_bounds__(kThreads, kMethod == BG_RESAMPLE_CATMULL_ROM ? 4 : 8)
     k_resample_grid(Src s, GridView o, int chunks,
                                                             float* __restrict__ out,
                                                             int8_t* __restrict__ how_out) {
