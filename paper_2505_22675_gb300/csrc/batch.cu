@@ -55,6 +55,7 @@ namespace {
 constexpr int kChunk = 4096;      // soundings per block in the per-sounding kernels
 constexpr int kBT = 256;          // threads of those kernels
 constexpr int kItemThreads = 128;
+constexpr int kKnnThreads = 64;  // k-NN blocks: a 16 KB heap, 13 blocks (26 warps) per SM
 constexpr int kBatchSolveBlocks = 8;  // solve blocks per claimed item: one atomic per 64 systems
 // The persistent solve reads its tile descriptor from shared memory, which
 // raises its register needs: it runs faster with 12 resident warps (no
@@ -257,12 +258,12 @@ __device__ __forceinline__ HashView tile_view(const TileDesc& d, const int4* ori
 }
 
 // 5. persistent k-NN items: IDW in place, kriging ids
-__global__ void __launch_bounds__(kItemThreads) k_batch_knn(
+__global__ void __launch_bounds__(kKnnThreads) k_batch_knn(
     const TileDesc* __restrict__ td, int T, const int64_t* __restrict__ item_off, int64_t items,
     unsigned long long* __restrict__ ctr, const int4* __restrict__ orig,
     const int4* __restrict__ rec, const int* __restrict__ cell_start, const int* __restrict__ sat,
     int* __restrict__ wide) {
-    __shared__ uint64_t heap[32 * kItemThreads];
+    __shared__ uint64_t heap[32 * kKnnThreads];
     __shared__ long long s_item;
     __shared__ int s_tile;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -281,32 +282,38 @@ __global__ void __launch_bounds__(kItemThreads) k_batch_knn(
         const HashView h = tile_view(d, orig, rec, cell_start, sat);
         const GridView g = d.g;
         const int64_t patch = item - __ldg(item_off + t);
-        const NodeIdx nd = patch_node((int)(patch % d.gx), (int)(patch / d.gx), warp, lane);
-        if (nd.i >= g.nx || nd.j >= g.ny) continue;
-        const int64_t node = (int64_t)nd.j * g.nx + nd.i;
-        const int qx = g.x0 + nd.i * g.cell + g.cell / 2;
-        const int qy = g.y0 + nd.j * g.cell + g.cell / 2;
-        const int k = d.k;
-        int keff = 0;
-        if (h.n_valid > 0) {
-            const Bound b = knn_bound_rt(h, qx, qy, d.method == 0 ? k : d.K);
-            if (!packed_fits(h, b.tau0)) {
-                *wide = 1;
-                continue;
+        // the 16 x 8 patch in two halves of 16 x 4 (two warps each)
+        for (int half = 0; half < 2; ++half) {
+            const NodeIdx nd = patch_node((int)(patch % d.gx), (int)(patch / d.gx), warp + 2 * half,
+                                          lane);
+            if (nd.i >= g.nx || nd.j >= g.ny) continue;
+            const int64_t node = (int64_t)nd.j * g.nx + nd.i;
+            const int qx = g.x0 + nd.i * g.cell + g.cell / 2;
+            const int qy = g.y0 + nd.j * g.cell + g.cell / 2;
+            const int k = d.k;
+            int keff = 0;
+            if (h.n_valid > 0) {
+                const Bound b = knn_bound_rt(h, qx, qy, d.method == 0 ? k : d.K);
+                if (!packed_fits(h, b.tau0)) {
+                    *wide = 1;
+                    continue;
+                }
+                keff = min(knn_scan_heap_rt<kKnnThreads>(h, qx, qy, b, hp,
+                                                         d.method == 0 ? k : d.K), k);
             }
-            keff = min(knn_scan_heap_rt<kItemThreads>(h, qx, qy, b, hp, d.method == 0 ? k : d.K), k);
-        }
-        const int bits = h.idx_bits;
-        const uint64_t mask = (1ull << bits) - 1;
-        if (d.method == 0) {
-            d.depth[node] = idw_from(h, keff, d.power, [&](int i, uint64_t& dd, int& ii) {
-                const uint64_t key = hp[i * kItemThreads];
-                dd = key >> bits;
-                ii = (int)(key & mask);
-            });
-        } else {
-            int32_t* o = d.ids + node * k;
-            for (int i = 0; i < k; ++i) o[i] = i < keff ? (int)(hp[i * kItemThreads] & mask) : -1;
+            const int bits = h.idx_bits;
+            const uint64_t mask = (1ull << bits) - 1;
+            if (d.method == 0) {
+                d.depth[node] = idw_from(h, keff, d.power, [&](int i, uint64_t& dd, int& ii) {
+                    const uint64_t key = hp[i * kKnnThreads];
+                    dd = key >> bits;
+                    ii = (int)(key & mask);
+                });
+            } else {
+                int32_t* o = d.ids + node * k;
+                for (int i = 0; i < k; ++i)
+                    o[i] = i < keff ? (int)(hp[i * kKnnThreads] & mask) : -1;
+            }
         }
     }
 }
@@ -471,10 +478,9 @@ void enqueue_batch(bg_batch_s* b, cudaStream_t st) {
                                                 b->d_rec);
     k_batch_sat<<<T, 128, 0, st>>>(b->d_desc, b->d_cell_start, b->d_sat);
     note_launches(6 + (n > 0 ? 3 : 0));
-    // persistent kernels: a few resident blocks per SM drain the item lists
-    const int persist = 152 * 8;
+    // persistent kernels: as many blocks as an SM keeps resident drain the item lists
     if (b->knn_items > 0) {
-        k_batch_knn<<<(unsigned)std::min<int64_t>(b->knn_items, persist), kItemThreads, 0, st>>>(
+        k_batch_knn<<<(unsigned)std::min<int64_t>(b->knn_items, 152 * 13), kKnnThreads, 0, st>>>(
             b->d_desc, T, b->d_item_off, b->knn_items, b->d_ctr, b->d_orig, b->d_rec,
             b->d_cell_start, b->d_sat, b->d_flags);
         k_batch_wide<<<(unsigned)std::min<int64_t>(b->knn_items, 152 * 4), kItemThreads, 0, st>>>(
@@ -485,7 +491,7 @@ void enqueue_batch(bg_batch_s* b, cudaStream_t st) {
     for (int gi = 0; gi < ng; ++gi) {
         const auto& G = b->groups[gi];
         if (G.items == 0) continue;
-        const unsigned grid = (unsigned)std::min<int64_t>(G.items, 152 * 6);
+        const unsigned grid = (unsigned)std::min<int64_t>(G.items, 152 * kBatchSolveBlocksPerSM);
         unsigned long long* ctr = b->d_ctr + 1 + gi;
 #define BG_SOLVE(KK)                                                                              \
     k_batch_solve<KK><<<grid, kSolveWarps * 32, 0, st>>>(b->d_desc, G.tiles, G.nt, G.off, G.items, \

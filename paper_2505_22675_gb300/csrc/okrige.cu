@@ -8,14 +8,18 @@
 namespace bg {
 namespace {
 
-// grid rows [j0, j1); j0 is a multiple of 8; a strip of kStrip nodes per thread
+// grid rows [j0, j1); j0 is a multiple of 8; a strip of kStrip nodes per thread.
+// 64-thread blocks: the 16 KB heap (K = 32) plus the per-block reserve lets
+// 13 blocks (26 warps) share an SM, against 6 blocks (24 warps) of 128.
 template <int K>
-__global__ void __launch_bounds__(128) k_knn_ids(HashView h, GridView g, int k, int j0, int j1,
-                                                 int32_t* __restrict__ ids, int* __restrict__ flag) {
-    __shared__ uint64_t heap[K * 128];
+__global__ void __launch_bounds__(64) k_knn_ids(HashView h, GridView g, int k, int j0, int j1,
+                                                int32_t* __restrict__ ids, int* __restrict__ flag) {
+    __shared__ uint64_t heap[K * 64];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int gx = (g.nx + 16 * kStrip - 1) / (16 * kStrip);
-    const NodeIdx o = strip_origin(blockIdx.x % gx, j0 / 8 + blockIdx.x / gx, warp, lane);
+    // (16 * kStrip) x 4 node patches: warp w covers columns w * 8 * kStrip ..
+    const int px = blockIdx.x % gx, py = j0 / 4 + blockIdx.x / gx;
+    const NodeIdx o{px * 16 * kStrip + warp * 8 * kStrip + (lane & 7) * kStrip, py * 4 + (lane >> 3)};
     if (o.j >= j1) return;
     uint64_t* hp = heap + threadIdx.x;
     int32_t* base = ids + ((int64_t)(o.j - j0) * g.nx) * k;
@@ -25,9 +29,9 @@ __global__ void __launch_bounds__(128) k_knn_ids(HashView h, GridView g, int k, 
         return;
     }
     const uint64_t mask = (1ull << h.idx_bits) - 1;
-    knn_strip<128>(h, g, K, o.i, o.j, hp, flag, [&](int i, int cnt) {
+    knn_strip<64>(h, g, K, o.i, o.j, hp, flag, [&](int i, int cnt) {
         int32_t* out = base + (int64_t)i * k;
-        for (int q = 0; q < k; ++q) out[q] = q < cnt ? (int)(hp[q * 128] & mask) : -1;
+        for (int q = 0; q < k; ++q) out[q] = q < cnt ? (int)(hp[q * 64] & mask) : -1;
     });
 }
 
@@ -75,7 +79,7 @@ bg_status launch_k(const HashView& h, const GridView& g, int k, const OkParams& 
     for (int64_t j0 = 0; j0 < g.ny; j0 += rows) {
         const int64_t j1 = std::min<int64_t>(g.ny, j0 + rows);
         const int64_t nb = (int64_t)gx * ((j1 - j0 + 7) / 8);
-        const int64_t nbs = (int64_t)((g.nx + 16 * kStrip - 1) / (16 * kStrip)) * ((j1 - j0 + 7) / 8);
+        const int64_t nbs = (int64_t)((g.nx + 16 * kStrip - 1) / (16 * kStrip)) * ((j1 - j0 + 3) / 4);
         int32_t* chunk_ids = nbr ? nbr + j0 * g.nx * k : (int32_t*)((char*)scratch + flag_bytes);
         cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), st);
         if (e != cudaSuccess) {
@@ -85,7 +89,7 @@ bg_status launch_k(const HashView& h, const GridView& g, int k, const OkParams& 
         const int64_t nodes = (j1 - j0) * g.nx;
         {
             ProfScope ps(ctx, kProfKnnIds, nodes, st);
-            k_knn_ids<K><<<(unsigned)nbs, 128, 0, st>>>(h, g, k, (int)j0, (int)j1, chunk_ids, flag);
+            k_knn_ids<K><<<(unsigned)nbs, 64, 0, st>>>(h, g, k, (int)j0, (int)j1, chunk_ids, flag);
         }
         k_knn_ids_wide<K><<<(unsigned)std::min<int64_t>(nb, 152 * 4), 128, 0, st>>>(
             h, g, k, (int)j0, (int)j1, chunk_ids, flag);
