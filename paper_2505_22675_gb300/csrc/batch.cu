@@ -707,6 +707,7 @@ bg_status bg_batch_create(bg_ctx_t ctx, const bg_tile* tiles, int n_tiles, bg_ba
 }
 
 bg_status bg_batch_run(bg_batch_t b, void* cuda_stream) {
+    bg::NvtxRange nvtx("bg_batch_run");
     if (!b) {
         set_error("batch is NULL");
         return BG_ERR_INVALID_ARG;

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <atomic>
 #include <mutex>
 #include <string>
@@ -48,6 +50,15 @@ struct HashView {
 
 struct GridView {
     int32_t x0, y0, cell, nx, ny;
+};
+
+// A named range on the host timeline of a profiler (NVTX; header-only, a no-op
+// unless a tool is attached): one per entry point that enqueues work.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
 };
 
 // IDW fused into a kriging pass: depth over the first k of the kriging's

@@ -277,6 +277,7 @@ bg_status bg_grid_destroy(bg_grid_t grid) {
 bg_status bg_soundings_upload(bg_ctx_t ctx, const int32_t* x_cm, const int32_t* y_cm,
                               const float* z_m, int64_t n, int on_device, int32_t cell_cm_hint,
                               void* cuda_stream, bg_soundings_t* out) {
+    bg::NvtxRange nvtx("bg_soundings_upload");
     BG_REQUIRE(ctx && out, "NULL argument");
     *out = nullptr;
     BG_REQUIRE(n >= 0 && n < ((int64_t)1 << 31) - 1, "n must be in [0, 2^31 - 1)");
@@ -333,6 +334,7 @@ static bg_status check_interp(bg_soundings_t s, bg_grid_t grid, int k, float* de
 
 bg_status bg_interp_idw(bg_soundings_t s, bg_grid_t grid, int k, float power, float* depth_out,
                         int32_t* nbr_out, void* cuda_stream) {
+    bg::NvtxRange nvtx("bg_interp_idw");
     bg_status rc = check_interp(s, grid, k, depth_out);
     if (rc != BG_OK) return rc;
     BG_REQUIRE(finite_pos(power), "power must be finite and > 0");
@@ -356,6 +358,7 @@ static bool okrige_params(const bg_variogram* v, OkParams* p) {
 
 bg_status bg_interp_okrige(bg_soundings_t s, bg_grid_t grid, int k, const bg_variogram* v,
                            float* depth_out, float* var_out, int32_t* nbr_out, void* cuda_stream) {
+    bg::NvtxRange nvtx("bg_interp_okrige");
     bg_status rc = check_interp(s, grid, k, depth_out);
     if (rc != BG_OK) return rc;
     OkParams p;
@@ -369,6 +372,7 @@ bg_status bg_interp_okrige(bg_soundings_t s, bg_grid_t grid, int k, const bg_var
 bg_status bg_interp_idw_okrige(bg_soundings_t s, bg_grid_t grid, int k_idw, float power,
                                int k_okrige, const bg_variogram* v, float* idw_out,
                                float* depth_out, float* var_out, void* cuda_stream) {
+    bg::NvtxRange nvtx("bg_interp_idw_okrige");
     bg_status rc = check_interp(s, grid, k_okrige, depth_out);
     if (rc != BG_OK) return rc;
     BG_REQUIRE(idw_out, "idw_out is NULL");
@@ -399,6 +403,7 @@ static bg_status check_points(bg_soundings_t s, const int32_t* qx, const int32_t
 bg_status bg_interp_idw_points(bg_soundings_t s, const int32_t* qx_cm, const int32_t* qy_cm,
                                int64_t m, int k, float power, float* depth_out, int32_t* nbr_out,
                                void* cuda_stream) {
+    bg::NvtxRange nvtx("bg_interp_idw_points");
     bg_status rc = check_points(s, qx_cm, qy_cm, m, k, depth_out);
     if (rc != BG_OK) return rc;
     BG_REQUIRE(finite_pos(power), "power must be finite and > 0");
@@ -411,6 +416,7 @@ bg_status bg_interp_idw_points(bg_soundings_t s, const int32_t* qx_cm, const int
 bg_status bg_interp_okrige_points(bg_soundings_t s, const int32_t* qx_cm, const int32_t* qy_cm,
                                   int64_t m, int k, const bg_variogram* v, float* depth_out,
                                   float* var_out, int32_t* nbr_out, void* cuda_stream) {
+    bg::NvtxRange nvtx("bg_interp_okrige_points");
     bg_status rc = check_points(s, qx_cm, qy_cm, m, k, depth_out);
     if (rc != BG_OK) return rc;
     OkParams p;
@@ -436,6 +442,7 @@ bg_status bg_resample_points(const float* src, int32_t x0_cm, int32_t y0_cm, int
                              int32_t nx, int32_t ny, int method, const int32_t* qx_cm,
                              const int32_t* qy_cm, int64_t m, float* out, int8_t* how_out,
                              void* cuda_stream) {
+    bg::NvtxRange nvtx("bg_resample_points");
     bg_status rc = check_source(src, x0_cm, y0_cm, cell_cm, nx, ny, method);
     if (rc != BG_OK) return rc;
     BG_REQUIRE(m >= 0 && m < ((int64_t)1 << 40), "m must be in [0, 2^40)");
@@ -448,6 +455,7 @@ bg_status bg_resample_grid(const float* src, int32_t x0_cm, int32_t y0_cm, int32
                            int32_t nx, int32_t ny, int method, int32_t ox0_cm, int32_t oy0_cm,
                            int32_t ocell_cm, int32_t onx, int32_t ony, float* out,
                            int8_t* how_out, void* cuda_stream) {
+    bg::NvtxRange nvtx("bg_resample_grid");
     bg_status rc = check_source(src, x0_cm, y0_cm, cell_cm, nx, ny, method);
     if (rc != BG_OK) return rc;
     BG_REQUIRE(out, "out is NULL");

@@ -122,6 +122,7 @@ bg_status grow_pinned(void** p, size_t* have, size_t need) {
 
 // Issue one request on its slot (dispatcher thread, server lock not held).
 bg_status launch_request(Server* sv, Slot* sl, Ticket* t) {
+    NvtxRange nvtx("serve request");
     bg_ctx_s* ctx = sv->ctx;
     const bg_request& r = t->req;
     const int64_t n = r.n, m = t->nodes;

@@ -27,6 +27,13 @@ import numpy as np
 IDW = 0
 OKRIGE = 1
 
+
+class RankFailure(RuntimeError):
+    """A collective of the partitioning failed: a rank left the group, timed
+    out or raised. Ranks leave only between steps (no kernel of theirs is in
+    flight); the others learn of it here, at their next collective, within
+    the process group's timeout."""
+
 # relative cost per node of the two methods (kriging k=32 vs IDW k=16, measured
 # on one GB300: about 10x); used only to balance tile assignments
 METHOD_COST = {IDW: 1.0, OKRIGE: 10.0}
@@ -71,13 +78,20 @@ def assign_tiles(costs: Sequence[float], world: int) -> list[int]:
 
 # --------------------------------------------------------------- collectives
 
+def _collective(fn, *args, **kwargs):
+    try:
+        return fn(*args, **kwargs)
+    except Exception as e:  # the backend's own error types differ
+        raise RankFailure(f"collective {getattr(fn, '__name__', fn)} failed: {e}") from e
+
+
 def _broadcast_array(dist, arr, src, group, dtype):
     import torch
     n = torch.tensor([0 if arr is None else arr.size], dtype=torch.int64)
-    dist.broadcast(n, src, group=group)
+    _collective(dist.broadcast, n, src, group=group)
     t = torch.from_numpy(np.ascontiguousarray(arr)) if arr is not None and dist.get_rank(group) == src \
         else torch.empty(int(n.item()), dtype=dtype)
-    dist.broadcast(t, src, group=group)
+    _collective(dist.broadcast, t, src, group=group)
     return t.numpy()
 
 
@@ -87,12 +101,12 @@ def _gather_to_root(dist, piece: np.ndarray, group, root=0):
     world = dist.get_world_size(group)
     n = torch.tensor([piece.size], dtype=torch.int64)
     sizes = [torch.zeros(1, dtype=torch.int64) for _ in range(world)]
-    dist.all_gather(sizes, n, group=group)
+    _collective(dist.all_gather, sizes, n, group=group)
     m = max(int(s.item()) for s in sizes)
     buf = torch.zeros(m, dtype=torch.from_numpy(piece[:0]).dtype)
     buf[:piece.size] = torch.from_numpy(piece)
     parts = [torch.zeros_like(buf) for _ in range(world)]
-    dist.all_gather(parts, buf, group=group)
+    _collective(dist.all_gather, parts, buf, group=group)
     if dist.get_rank(group) != root:
         return None
     return np.concatenate([p[:int(s.item())].numpy() for p, s in zip(parts, sizes)])
@@ -185,7 +199,7 @@ def grid_tiles(tiles, group=None, compute: Callable | None = None, root: int = 0
     # every rank knows every owner, so rank-major order is reproducible on root
     sizes = torch.tensor([flat.size], dtype=torch.int64)
     per_rank = [torch.zeros(1, dtype=torch.int64) for _ in range(world)]
-    dist.all_gather(per_rank, sizes, group=group)
+    _collective(dist.all_gather, per_rank, sizes, group=group)
     if rank != root:
         return None
     out = [None] * len(tiles)

@@ -123,3 +123,36 @@ def test_slabs_on_one_gpu_equal_the_unsplit_grid():
             if method == D.OKRIGE:
                 v = np.concatenate([p[1] for p in parts])
                 assert np.array_equal(v.view(np.uint32), full_v.view(np.uint32))
+
+
+def _rank_leaves(rank, world, port, out_dir):
+    import datetime
+
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world,
+                            timeout=datetime.timedelta(seconds=20))
+    if rank == 1:
+        os._exit(0)  # leaves between steps: none of its collectives is in flight
+    w = synth.swath(seed=2, lines=2, pings=40, beams=32)
+    g = w.grid
+    outcome = "no error"
+    try:
+        D.grid_swath(w.x_cm, w.y_cm, w.z_m, (g.x0_cm, g.y0_cm, g.cell_cm, g.nx, g.ny), D.IDW, 8,
+                     compute=oracle_compute)
+    except D.RankFailure:
+        outcome = "rank failure"
+    with open(os.path.join(out_dir, "rank0.txt"), "w") as f:
+        f.write(outcome)
+    os._exit(0)  # the group is broken: no orderly teardown
+
+
+def test_a_rank_that_leaves_is_reported_not_waited_for(tmp_path):
+    import time
+
+    import torch.multiprocessing as mp
+    t0 = time.time()
+    mp.spawn(_rank_leaves, args=(2, _free_port(), str(tmp_path)), nprocs=2, join=True)
+    assert (tmp_path / "rank0.txt").read_text() == "rank failure"
+    assert time.time() - t0 < 120
