@@ -297,11 +297,10 @@ __device__ __forceinline__ int knn_scan_heap_rt(const HashView& h, int qx, int q
         const int s = __ldg(h.cell_start + rowbase + ca);
         const int e = __ldg(h.cell_start + rowbase + cb + 1);
         const uint64_t utau = (uint64_t)tau;
-        for (int p = s; p < e; ++p) {
-            const int4 v = __ldg(h.rec + p);
+        auto take = [&](const int4 v) {
             const int ddx = v.x - qx, ddy = v.y - qy;
             const uint64_t d2 = (uint64_t)((long long)ddx * ddx + (long long)ddy * ddy);
-            if (d2 > utau) continue;
+            if (d2 > utau) return;
             const uint64_t c = (d2 << bits) | (uint32_t)v.w;
             if (c < root) {
                 if (cnt < kc) {
@@ -315,7 +314,15 @@ __device__ __forceinline__ int knn_scan_heap_rt(const HashView& h, int qx, int q
                     root = hp[0];
                 }
             }
+        };
+        // two records in flight at a time (the run's loads do not depend on the heap)
+        int p = s;
+        for (; p + 1 < e; p += 2) {
+            const int4 v0 = __ldg(h.rec + p), v1 = __ldg(h.rec + p + 1);
+            take(v0);
+            take(v1);
         }
+        if (p < e) take(__ldg(h.rec + p));
         tau = min(tau, (int64_t)(root >> bits));
     }
     // heapsort into ascending order
