@@ -423,6 +423,29 @@ def gridded_measure(bg, torch, n_side, fracs, steps=5):
     return out
 
 
+def gpu_local_affinity(device_index: int):
+    """Restrict this thread to the CPUs sysfs lists as local to the GPU (if any
+    of them are allowed); returns the previous CPU set to restore, or None."""
+    try:
+        import torch
+        pr = torch.cuda.get_device_properties(device_index)
+        path = (f"/sys/bus/pci/devices/{pr.pci_domain_id:04x}:{pr.pci_bus_id:02x}:"
+                f"{pr.pci_device_id:02x}.0/local_cpulist")
+        cpus = set()
+        with open(path) as f:
+            for part in f.read().strip().split(","):
+                a, _, b = part.partition("-")
+                cpus.update(range(int(a), int(b or a) + 1))
+        saved = os.sched_getaffinity(0)
+        use = cpus & saved
+        if not use or use == saved:
+            return None
+        os.sched_setaffinity(0, use)
+        return saved
+    except (AttributeError, OSError, ValueError, RuntimeError):
+        return None
+
+
 def workload(args):
     if args.small:
         return synth.swath(seed=2, lines=2, pings=2000, beams=256)
@@ -581,7 +604,10 @@ def bench_ours(args):
         ms = float(t.item())
     value = ws * m / (ms / 1e3)
 
-    # ---- end to end through the C ABI with host buffers (pinned), copies timed
+    # ---- end to end through the C ABI with host buffers (pinned), copies timed.
+    # The host buffers are allocated (first touch) from the CPUs next to the GPU
+    # where the system says which those are, so that they sit in its NUMA node.
+    saved_cpus = gpu_local_affinity(local)
     xh, yh, zh = (torch.from_numpy(a).pin_memory() for a in (w.x_cm, w.y_cm, w.z_m))
     out_h = [torch.empty(m, pin_memory=True) for _ in range(3)]
 
@@ -609,6 +635,8 @@ def bench_ours(args):
         t = torch.tensor([e2e_ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_ms = float(t.item())
+    if saved_cpus is not None:
+        os.sched_setaffinity(0, saved_cpus)
     bad = int(torch.isnan(d_idw).sum() + torch.isnan(d_ok).sum())
 
     if rank == 0:

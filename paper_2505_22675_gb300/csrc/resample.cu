@@ -92,13 +92,15 @@ __device__ __forceinline__ void cr_weights(float t, float (&w)[4]) {
 // needed stencil nodes are read (predicated loads, no branches), so the loads
 // of a thread's queries overlap. how: 0 by the method, 1 by the bilinear
 // fallback, 2 no value.
-template <int kMethod>
+// kColX: every query of the launch lies on a node column (the row-filling
+// shape), so only the column case is compiled.
+template <int kMethod, bool kColX = false>
 __device__ __forceinline__ float resample_at(const Src& s, const Axis& ax, const Axis& ay,
                                              const float* const (&rows)[4], int8_t& how) {
     float f;
     const int i = ax.i;
     if constexpr (kMethod == BG_RESAMPLE_CATMULL_ROM) {
-        if (ax.r == 0 || ax.r == s.cell) {
+        if (kColX || ax.r == 0 || ax.r == s.cell) {
             // on a node column (the row-filling shape): one column of the stencil,
             // the same arithmetic as the general case with x weights (0, 1, 0, 0)
             const int a = ax.r == 0 ? 1 : 2;
@@ -226,11 +228,10 @@ __global__ void __launch_bounds__(kThreads) k_resample_pts(Src s, const int32_t*
 // source lattice (one integer division each) serve all its rows
 constexpr int kRowsPerBlock = 8;
 
-template <int kMethod>
+template <int kMethod, bool kColX>
 __global__ void __launch_bounds__(kThreads, kMethod == BG_RESAMPLE_CATMULL_ROM ? 4 : 8)
-    k_resample_grid(Src s, GridView o, int chunks,
-                                                            float* __restrict__ out,
-                                                            int8_t* __restrict__ how_out) {
+    k_resample_grid(Src s, GridView o, int chunks, float* __restrict__ out,
+                    int8_t* __restrict__ how_out) {
     const int band = blockIdx.x / chunks;
     const int c0 = (blockIdx.x - band * chunks) * kThreads * kPer + threadIdx.x;
     const int64_t ux0 = (int64_t)o.x0 + o.cell / 2 - s.cx0;
@@ -250,7 +251,7 @@ __global__ void __launch_bounds__(kThreads, kMethod == BG_RESAMPLE_CATMULL_ROM ?
         for (int k = 0; k < kPer; ++k) {
             const int c = c0 + k * kThreads;
             int8_t how;
-            const float f = resample_at<kMethod>(s, ax[k], ay, rows, how);
+            const float f = resample_at<kMethod, kColX>(s, ax[k], ay, rows, how);
             if (c < o.nx) {
                 const int64_t p = (int64_t)row * o.nx + c;
                 out[p] = f;
@@ -289,12 +290,21 @@ bg_status launch_resample_grid(const float* src, const GridView& g, int method, 
         set_error("output grid too large for one launch");
         return BG_ERR_INVALID_ARG;
     }
-    if (method == BG_RESAMPLE_CATMULL_ROM)
-        k_resample_grid<BG_RESAMPLE_CATMULL_ROM><<<(unsigned)blocks, kThreads, 0, st>>>(s, o, chunks,
-                                                                                      out, how);
-    else
-        k_resample_grid<BG_RESAMPLE_BILINEAR><<<(unsigned)blocks, kThreads, 0, st>>>(s, o, chunks,
-                                                                                   out, how);
+    // output columns on node columns of the source: the column case only
+    const int64_t off = (int64_t)o.x0 + o.cell / 2 - s.cx0;
+    const bool colx = o.cell % s.cell == 0 && ((off % s.cell) + s.cell) % s.cell == 0;
+    const unsigned nb = (unsigned)blocks;
+    if (method == BG_RESAMPLE_CATMULL_ROM) {
+        if (colx)
+            k_resample_grid<BG_RESAMPLE_CATMULL_ROM, true><<<nb, kThreads, 0, st>>>(s, o, chunks, out, how);
+        else
+            k_resample_grid<BG_RESAMPLE_CATMULL_ROM, false><<<nb, kThreads, 0, st>>>(s, o, chunks, out, how);
+    } else {
+        if (colx)
+            k_resample_grid<BG_RESAMPLE_BILINEAR, true><<<nb, kThreads, 0, st>>>(s, o, chunks, out, how);
+        else
+            k_resample_grid<BG_RESAMPLE_BILINEAR, false><<<nb, kThreads, 0, st>>>(s, o, chunks, out, how);
+    }
     note_launches(1);
     BG_CUDA(cudaGetLastError());
     return BG_OK;
