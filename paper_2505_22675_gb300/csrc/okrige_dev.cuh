@@ -100,6 +100,40 @@ __device__ __forceinline__ float gamma_pair_f(const OkParams& p, float dx, float
     return fmaf(p.c, -expm1f(-h_cm * p.inv_a * 0.01f), p.c0);
 }
 
+// one hardware square-root approximation (sqrt.approx.f32: a few ulp, 0 at 0)
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float y;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// The variogram of the assembly in the fixed-point scale of the system: with
+// the scale sa a power of two, sa gamma(h) is the model with c0 and c scaled
+// by sa. t^2 = d2 (1/a)^2 from the exact squared separation in cm^2.
+struct ScaledVgm {
+    float kinv2;  // (0.01 / a)^2: cm^2 -> (h / a)^2
+    float c0s;    // sa c0
+    float cs;     // sa c
+    float k2, k3; // spherical: -0.5 sa c, 1.5 sa c
+};
+
+__device__ __forceinline__ ScaledVgm scaled_vgm(const OkParams& p, float sa) {
+    const float kinv = p.inv_a * 0.01f;
+    const float cs = p.c * sa;
+    return ScaledVgm{kinv * kinv, p.c0 * sa, cs, -0.5f * cs, 1.5f * cs};
+}
+
+template <bool kSpherical>
+__device__ __forceinline__ float gamma_pair_scaled(const ScaledVgm& v, float dx, float dy) {
+    const float t2 = fmaf(dx, dx, dy * dy) * v.kinv2;
+    if constexpr (kSpherical) {
+        const float t = fminf(sqrt_approx(t2), 1.0f);  // the polynomial is the sill at t = 1
+        return fmaf(t, fmaf(v.k2, t * t, v.k3), v.c0s);
+    } else {
+        return fmaf(v.cs, -expm1f(-sqrt_approx(t2)), v.c0s);
+    }
+}
+
 // ------------------------------------------------------------ k-NN -> ids
 
 template <int K, bool kWide>
@@ -373,7 +407,6 @@ __device__ __forceinline__ void okrige_solve_block(const HashView& h, const Grid
             zr[s] = __int_as_float(rr.z);
             gr0[s] = real ? gamma_pair_f(p, ox, oy) : 0.0f;
             g0r[s] = real ? gamma_cm(p, rr.x - qx, rr.y - qy, 0.0f) : 0.0f;
-            tg[r] = gr0[s];
             gmax = fmaxf(gmax, gr0[s]);
         }
 #pragma unroll
@@ -403,29 +436,63 @@ __device__ __forceinline__ void okrige_solve_block(const HashView& h, const Grid
         // fixed point with 30 bits below that bound
         const int ea = 30 - exp_above(fmaxf(1.0f, 2.0f * gmax));
         const float sa = pow2f(ea), isa = pow2f(-ea);
+#pragma unroll
+        for (int s = 0; s < kR; ++s) tg[G * s + t] = gr0[s] * sa;  // Gamma_r0 in the fixed-point scale
+        const ScaledVgm sv = scaled_vgm(p, sa);
         __syncwarp();
 
         // assemble the lower triangle once per entry, straight into fixed
-        // point: thread t owns the columns c = t + G q; for each it walks the
-        // rows r >= G q in step with its group (rows above its column idle),
-        // so a row's entries land in consecutive banks and the unrolled walk
-        // gives the thread independent entries to overlap
+        // point. Every term is in the fixed-point scale already (tg and the
+        // scaled variogram), so an entry is one rounding to integer. The
+        // triangle splits into G x G blocks: below the diagonal blocks,
+        // thread t owns the columns c = t + G q and the group walks the rows
+        // in step (a row's entries land in consecutive banks); the
+        // G (G + 1) / 2 entries of a diagonal block are dealt out to the
+        // group's threads in turn, so no thread idles above its column.
+        auto entry = [&](auto spherical, int r, int c) {
+            constexpr bool kSph = decltype(spherical)::value;
+            const float gc = tg[c];
+            // a real row r (r + 1 < ke) implies a real column c < r
+            const float v =
+                (r == c) ? ((c + 1 < ke) ? 2.0f * gc : sa)
+                : (r + 1 < ke)
+                    ? (tg[r] + gc) - gamma_pair_scaled<kSph>(sv, fx[r + 1] - fx[c + 1], fy[r + 1] - fy[c + 1])
+                    : 0.0f;
+            Aq[tri(r) + c] = __float2int_rn(v);
+        };
+        constexpr int kDiag = G * (G + 1) / 2, kDiagSlots = (kDiag + G - 1) / G;
+        int dij[kDiagSlots];  // (row, column) in a diagonal block of this thread's slots
 #pragma unroll
-        for (int q = 0; q < kR; ++q) {
-            const int c = t + G * q;
-            const float xc = fx[c + 1], yc = fy[c + 1], gcc = tg[c];
-            const float dg = (c + 1 < ke) ? 2.0f * gcc : 1.0f;
-#pragma unroll 4
-            for (int r = G * q; r < K; ++r) {
-                if (r < c) continue;
-                // a real row r (r + 1 < ke) implies a real column c < r
-                const float v = (r == c) ? dg
-                                : (r + 1 < ke)
-                                    ? (tg[r] + gcc) - gamma_pair_f(p, fx[r + 1] - xc, fy[r + 1] - yc)
-                                    : 0.0f;
-                Aq[tri(r) + c] = __float2int_rn(v * sa);
-            }
+        for (int m = 0; m < kDiagSlots; ++m) {
+            const int e = t + G * m;
+            int i = 0;
+            while (tri(i + 1) <= e) ++i;
+            dij[m] = (i << 8) | (e - tri(i));
         }
+        auto assemble = [&](auto spherical) {
+            constexpr bool kSph = decltype(spherical)::value;
+#pragma unroll
+            for (int q = 0; q < kR; ++q) {
+#pragma unroll
+                for (int m = 0; m < kDiagSlots; ++m)
+                    if (kDiag % G == 0 || m + 1 < kDiagSlots || t + G * m < kDiag)
+                        entry(spherical, G * q + (dij[m] >> 8), G * q + (dij[m] & 0xff));
+                const int c = t + G * q;
+                const float xc = fx[c + 1], yc = fy[c + 1], gcc = tg[c];
+#pragma unroll 4
+                for (int r = G * (q + 1); r < K; ++r) {
+                    const float v =
+                        (r + 1 < ke)
+                            ? (tg[r] + gcc) - gamma_pair_scaled<kSph>(sv, fx[r + 1] - xc, fy[r + 1] - yc)
+                            : 0.0f;
+                    Aq[tri(r) + c] = __float2int_rn(v);
+                }
+            }
+        };
+        if (p.model == BG_VARIOGRAM_SPHERICAL)
+            assemble(std::true_type{});
+        else
+            assemble(std::false_type{});
         __syncwarp();
 
         // my rows into registers (zero above the diagonal)
