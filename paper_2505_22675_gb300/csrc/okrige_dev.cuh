@@ -278,25 +278,36 @@ __device__ __forceinline__ void fwd_step(const float (&L)[Geo<K>::LEN], const fl
         if (G * (s + 1) - 1 > J && G * s + t > J) v[s] = fmaf(-L[Gm::off(s) + J], yj, v[s]);
 }
 
-// back sweep for column J = K-1-I of L^T x = y in dot-product form: each
-// thread sums L[r][J] x_r over its solved rows r > J (its register rows of
-// L), the group adds the partial sums (xor shuffles), and the owner of row J
-// finishes x_J. No transposed copy of the factor is kept, which holds the
-// shared memory per system to the packed A and the tables.
+// back sweep for column J = K-1-I of L^T x = y in dot-product form, software
+// pipelined by one column: x_J = (y_J - P_J - L[J+1][J] x_{J+1}) / L[J][J],
+// where P_J = sum over rows r > J+1 of L[r][J] x_r. Each thread sums its
+// register rows of L (no transposed copy of the factor), the group adds the
+// partial sums by xor shuffles, and P_J is reduced one step ahead (its rows
+// are solved before x_{J+1} is), so that reduction overlaps the finishing of
+// x_{J+1}; the one term that needs x_{J+1} comes from its owner by one
+// shuffle. pj carries P_J into the step and P_{J-1} out of it.
 template <int K, int I>
 __device__ __forceinline__ void bwd_step(const float (&L)[Geo<K>::LEN], const float (&dinv)[kR],
-                                         float (&v)[kR], int t) {
+                                         float (&v)[kR], int t, int gbase, float& pj) {
     using Gm = Geo<K>;
     constexpr int G = Gm::G;
     constexpr int J = K - 1 - I;
     constexpr int SJ = J / G;
-    float part = 0.0f;
+    float dj = 0.0f;
+    if constexpr (J + 1 < K) {
+        constexpr int S1 = (J + 1) / G;
+        dj = __shfl_sync(kFull, L[Gm::off(S1) + J] * v[S1], gbase + (J + 1) % G);
+    }
+    float pn = 0.0f;
+    if constexpr (J > 0) {
 #pragma unroll
-    for (int s = 0; s < kR; ++s)
-        if (G * (s + 1) - 1 > J) part = (G * s + t > J) ? fmaf(L[Gm::off(s) + J], v[s], part) : part;
+        for (int s = 0; s < kR; ++s)
+            if (G * (s + 1) - 1 > J) pn = (G * s + t > J) ? fmaf(L[Gm::off(s) + J - 1], v[s], pn) : pn;
 #pragma unroll
-    for (int o = 1; o < G; o <<= 1) part += __shfl_xor_sync(kFull, part, o);
-    if (t == J % G) v[SJ] = (v[SJ] - part) * dinv[SJ];
+        for (int o = 1; o < G; o <<= 1) pn += __shfl_xor_sync(kFull, pn, o);
+    }
+    if (t == J % G) v[SJ] = ((v[SJ] - pj) - dj) * dinv[SJ];
+    pj = pn;
 }
 
 template <int K, int... J>
@@ -304,7 +315,8 @@ __device__ __forceinline__ void chol_solve_seq(const float (&L)[Geo<K>::LEN],
                                                const float (&dinv)[kR], float (&v)[kR], int t,
                                                int gbase, std::integer_sequence<int, J...>) {
     (fwd_step<K, J>(L, dinv, v, t, gbase), ...);
-    (bwd_step<K, J>(L, dinv, v, t), ...);
+    float pj = 0.0f;
+    (bwd_step<K, J>(L, dinv, v, t, gbase, pj), ...);
 }
 
 // 2^e as a float (|e| <= 126)
