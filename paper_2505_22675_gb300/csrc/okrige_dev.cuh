@@ -47,6 +47,7 @@ constexpr int kR = 4;            // rows per thread
 constexpr int kSolveWarps = 4;   // warps per solve block
 constexpr int kRounds = 1;       // system batches per warp (one: more, shorter blocks balance best)
 constexpr int kSolveBlocksPerSM = 4;  // launch bound: 16 warps resident (128 registers)
+constexpr int kBwdLook = 2;      // back-sweep pipeline depth (see bwd_step)
 
 template <int K>
 struct Geo {
@@ -279,44 +280,60 @@ __device__ __forceinline__ void fwd_step(const float (&L)[Geo<K>::LEN], const fl
 }
 
 // back sweep for column J = K-1-I of L^T x = y in dot-product form, software
-// pipelined by one column: x_J = (y_J - P_J - L[J+1][J] x_{J+1}) / L[J][J],
-// where P_J = sum over rows r > J+1 of L[r][J] x_r. Each thread sums its
-// register rows of L (no transposed copy of the factor), the group adds the
-// partial sums by xor shuffles, and P_J is reduced one step ahead (its rows
-// are solved before x_{J+1} is), so that reduction overlaps the finishing of
-// x_{J+1}; the one term that needs x_{J+1} comes from its owner by one
-// shuffle. pj carries P_J into the step and P_{J-1} out of it.
-template <int K, int I>
+// pipelined: each thread sums its register rows of L (no transposed copy of
+// the factor) and the group adds the partial sums by xor shuffles, but the
+// sum over the rows far below J is reduced kLook steps ahead, so that its
+// shuffles overlap the finishing of the columns in between; the terms of the
+// kLook rows just below J come from their owners by one shuffle each.
+//   kLook = 1: x_J = (y_J - P_J - L[J+1][J] x_{J+1}) / L[J][J], P_J over rows > J+1
+//   kLook = 2: x_J = (y_J - Q_J - E_J - L[J+1][J] x_{J+1}) / L[J][J], Q_J over
+//              rows > J+2, E_J = L[J+2][J] x_{J+2} (sent one step early)
+// p0 carries the far sum for column J into the step; p1 and e0 (kLook = 2)
+// carry Q_{J-1} and E_{J-1}. Every kernel takes the same depth (kBwdLook), so
+// the fused IDW + kriging pass stays bitwise equal to the kriging call.
+template <int K, int kLook, int I>
 __device__ __forceinline__ void bwd_step(const float (&L)[Geo<K>::LEN], const float (&dinv)[kR],
-                                         float (&v)[kR], int t, int gbase, float& pj) {
+                                         float (&v)[kR], int t, int gbase, float& p0, float& p1,
+                                         float& e0) {
+    static_assert(kLook == 1 || kLook == 2, "pipeline depth");
     using Gm = Geo<K>;
     constexpr int G = Gm::G;
     constexpr int J = K - 1 - I;
     constexpr int SJ = J / G;
-    float dj = 0.0f;
+    float dj = 0.0f, en = 0.0f;
     if constexpr (J + 1 < K) {
         constexpr int S1 = (J + 1) / G;
         dj = __shfl_sync(kFull, L[Gm::off(S1) + J] * v[S1], gbase + (J + 1) % G);
+        if constexpr (kLook == 2 && J > 0)
+            en = __shfl_sync(kFull, L[Gm::off(S1) + J - 1] * v[S1], gbase + (J + 1) % G);
     }
+    // far sum for column J - kLook over the rows > J (all solved)
     float pn = 0.0f;
-    if constexpr (J > 0) {
+    if constexpr (J >= kLook) {
 #pragma unroll
         for (int s = 0; s < kR; ++s)
-            if (G * (s + 1) - 1 > J) pn = (G * s + t > J) ? fmaf(L[Gm::off(s) + J - 1], v[s], pn) : pn;
+            if (G * (s + 1) - 1 > J)
+                pn = (G * s + t > J) ? fmaf(L[Gm::off(s) + J - kLook], v[s], pn) : pn;
 #pragma unroll
         for (int o = 1; o < G; o <<= 1) pn += __shfl_xor_sync(kFull, pn, o);
     }
-    if (t == J % G) v[SJ] = ((v[SJ] - pj) - dj) * dinv[SJ];
-    pj = pn;
+    if (t == J % G) v[SJ] = (((v[SJ] - p0) - e0) - dj) * dinv[SJ];
+    if constexpr (kLook == 1) {
+        p0 = pn;
+    } else {
+        p0 = p1;
+        p1 = pn;
+        e0 = en;
+    }
 }
 
-template <int K, int... J>
+template <int K, int kLook, int... J>
 __device__ __forceinline__ void chol_solve_seq(const float (&L)[Geo<K>::LEN],
                                                const float (&dinv)[kR], float (&v)[kR], int t,
                                                int gbase, std::integer_sequence<int, J...>) {
     (fwd_step<K, J>(L, dinv, v, t, gbase), ...);
-    float pj = 0.0f;
-    (bwd_step<K, J>(L, dinv, v, t, gbase, pj), ...);
+    float p0 = 0.0f, p1 = 0.0f, e0 = 0.0f;
+    (bwd_step<K, kLook, J>(L, dinv, v, t, gbase, p0, p1, e0), ...);
 }
 
 // 2^e as a float (|e| <= 126)
@@ -461,16 +478,14 @@ __device__ __forceinline__ void okrige_solve_block(const HashView& h, const Grid
         // in step (a row's entries land in consecutive banks); the
         // G (G + 1) / 2 entries of a diagonal block are dealt out to the
         // group's threads in turn, so no thread idles above its column.
-        auto entry = [&](auto spherical, int r, int c) {
+        auto entry_value = [&](auto spherical, int r, int c) {
             constexpr bool kSph = decltype(spherical)::value;
             const float gc = tg[c];
             // a real row r (r + 1 < ke) implies a real column c < r
-            const float v =
-                (r == c) ? ((c + 1 < ke) ? 2.0f * gc : sa)
-                : (r + 1 < ke)
-                    ? (tg[r] + gc) - gamma_pair_scaled<kSph>(sv, fx[r + 1] - fx[c + 1], fy[r + 1] - fy[c + 1])
-                    : 0.0f;
-            Aq[tri(r) + c] = __float2int_rn(v);
+            return (r == c) ? ((c + 1 < ke) ? 2.0f * gc : sa)
+                   : (r + 1 < ke)
+                       ? (tg[r] + gc) - gamma_pair_scaled<kSph>(sv, fx[r + 1] - fx[c + 1], fy[r + 1] - fy[c + 1])
+                       : 0.0f;
         };
         constexpr int kDiag = G * (G + 1) / 2, kDiagSlots = (kDiag + G - 1) / G;
         int dij[kDiagSlots];  // (row, column) in a diagonal block of this thread's slots
@@ -481,23 +496,37 @@ __device__ __forceinline__ void okrige_solve_block(const HashView& h, const Grid
             while (tri(i + 1) <= e) ++i;
             dij[m] = (i << 8) | (e - tri(i));
         }
+        // loads and arithmetic of a batch ahead of its stores: the stores to
+        // the triangle then never sit between one entry's loads and the next
         auto assemble = [&](auto spherical) {
             constexpr bool kSph = decltype(spherical)::value;
 #pragma unroll
             for (int q = 0; q < kR; ++q) {
+                float dv[kDiagSlots];
+#pragma unroll
+                for (int m = 0; m < kDiagSlots; ++m)
+                    dv[m] = (kDiag % G == 0 || m + 1 < kDiagSlots || t + G * m < kDiag)
+                                ? entry_value(spherical, G * q + (dij[m] >> 8), G * q + (dij[m] & 0xff))
+                                : 0.0f;
 #pragma unroll
                 for (int m = 0; m < kDiagSlots; ++m)
                     if (kDiag % G == 0 || m + 1 < kDiagSlots || t + G * m < kDiag)
-                        entry(spherical, G * q + (dij[m] >> 8), G * q + (dij[m] & 0xff));
+                        Aq[tri(G * q + (dij[m] >> 8)) + G * q + (dij[m] & 0xff)] = __float2int_rn(dv[m]);
                 const int c = t + G * q;
                 const float xc = fx[c + 1], yc = fy[c + 1], gcc = tg[c];
-#pragma unroll 4
-                for (int r = G * (q + 1); r < K; ++r) {
-                    const float v =
-                        (r + 1 < ke)
-                            ? (tg[r] + gcc) - gamma_pair_scaled<kSph>(sv, fx[r + 1] - xc, fy[r + 1] - yc)
-                            : 0.0f;
-                    Aq[tri(r) + c] = __float2int_rn(v);
+                constexpr int kB = 4;
+#pragma unroll
+                for (int r0 = G * (q + 1); r0 < K; r0 += kB) {
+                    float vb[kB];
+#pragma unroll
+                    for (int u = 0; u < kB; ++u) {
+                        const int r = r0 + u;
+                        vb[u] = (r + 1 < ke)
+                                    ? (tg[r] + gcc) - gamma_pair_scaled<kSph>(sv, fx[r + 1] - xc, fy[r + 1] - yc)
+                                    : 0.0f;
+                    }
+#pragma unroll
+                    for (int u = 0; u < kB; ++u) Aq[tri(r0 + u) + c] = __float2int_rn(vb[u]);
                 }
             }
         };
@@ -540,7 +569,7 @@ __device__ __forceinline__ void okrige_solve_block(const HashView& h, const Grid
         for (int s = 0; s < kR; ++s) v[s] = b[s];
 #pragma unroll 1
         for (int pass = 0; pass < 2; ++pass) {
-            chol_solve_seq<K>(L, dinv, v, t, gbase, std::make_integer_sequence<int, K>{});
+            chol_solve_seq<K, kBwdLook>(L, dinv, v, t, gbase, std::make_integer_sequence<int, K>{});
             if (pass == 1) {
 #pragma unroll
                 for (int s = 0; s < kR; ++s) x[s] += v[s];
