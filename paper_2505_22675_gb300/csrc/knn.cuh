@@ -65,6 +65,31 @@ __device__ __forceinline__ int sat_count(const HashView& h, int xa, int ya, int 
            __ldg(s + (yb + 1) * W + xa) + __ldg(s + ya * W + xa);
 }
 
+// Number of rows beyond `row` in direction dir (+1 up, -1 down) that hold no
+// sounding within cell columns [ca, cb], up to `limit` rows: doubling then
+// bisection over summed-area-table counts of the band next to the row.
+__device__ __forceinline__ int empty_rows_beyond(const HashView& h, int row, int dir, int ca,
+                                                 int cb, int limit) {
+    auto band_empty = [&](int m) {  // rows row+dir .. row+dir*m
+        const int ra = dir > 0 ? row + 1 : row - m, rb = dir > 0 ? row + m : row - 1;
+        return sat_count(h, ca, ra, cb, rb) == 0;
+    };
+    int lo = 0, hi = 1;  // band of lo rows empty; band of hi rows not (or past limit)
+    while (hi <= limit && band_empty(hi)) {
+        lo = hi;
+        hi = 2 * hi;
+    }
+    hi = min(hi, limit + 1);
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (band_empty(mid))
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
 struct Bound {
     int64_t tau0;   // d_K^2 <= tau0
     int cy;         // the node's (clamped) cell row
@@ -296,6 +321,19 @@ __device__ __forceinline__ int knn_scan_heap_rt(const HashView& h, int qx, int q
         const int rowbase = row * h.ncx;
         const int s = __ldg(h.cell_start + rowbase + ca);
         const int e = __ldg(h.cell_start + rowbase + cb + 1);
+        if (s == e) {
+            // an empty run (a node in a gap of the coverage): the rows beyond it
+            // in this direction have runs within [ca, cb] (tau only shrinks and
+            // dy grows), so skip the ones the table shows empty over [ca, cb]
+            const int avail = take_up ? h.ncy - 1 - row : row;
+            const int within = (int)min((int64_t)avail, isqrt_ub(tau) / h.cs + 1);
+            const int skip = empty_rows_beyond(h, row, take_up ? 1 : -1, ca, cb, within);
+            if (take_up)
+                up += skip;
+            else
+                dn -= skip;
+            continue;
+        }
         const uint64_t utau = (uint64_t)tau;
         auto take = [&](const int4 v) {
             const int ddx = v.x - qx, ddy = v.y - qy;
