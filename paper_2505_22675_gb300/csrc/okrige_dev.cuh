@@ -464,7 +464,7 @@ __device__ __forceinline__ void okrige_solve_block(const HashView& h, const Grid
         // A is SPD, so |A[r][c]| <= its largest diagonal entry max(1, 2 max Gamma_r0);
         // fixed point with 30 bits below that bound
         const int ea = 30 - exp_above(fmaxf(1.0f, 2.0f * gmax));
-        const float sa = pow2f(ea), isa = pow2f(-ea);
+        const float sa = pow2f(ea);
 #pragma unroll
         for (int s = 0; s < kR; ++s) tg[G * s + t] = gr0[s] * sa;  // Gamma_r0 in the fixed-point scale
         const ScaledVgm sv = scaled_vgm(p, sa);
@@ -536,7 +536,9 @@ __device__ __forceinline__ void okrige_solve_block(const HashView& h, const Grid
             assemble(std::false_type{});
         __syncwarp();
 
-        // my rows into registers (zero above the diagonal)
+        // my rows into registers (zero above the diagonal), in the fixed-point
+        // scale: the factor is that of sa A, and the solves scale their
+        // right-hand sides by sa to match, so x comes out in A's units
         float L[Gm::LEN];
         float b[kR];
 #pragma unroll
@@ -550,7 +552,7 @@ __device__ __forceinline__ void okrige_solve_block(const HashView& h, const Grid
 #pragma unroll
             for (int c = 0; c < G * (s + 1); ++c) {
                 const int q = Aq[c <= r ? tri(r) + c : 0];
-                L[Gm::off(s) + c] = c <= r ? (float)q * isa : 0.0f;
+                L[Gm::off(s) + c] = c <= r ? (float)q : 0.0f;
             }
         }
 
@@ -566,7 +568,7 @@ __device__ __forceinline__ void okrige_solve_block(const HashView& h, const Grid
         // accumulated in 64-bit integers without rounding.
         float v[kR], x[kR];
 #pragma unroll
-        for (int s = 0; s < kR; ++s) v[s] = b[s];
+        for (int s = 0; s < kR; ++s) v[s] = b[s] * sa;
 #pragma unroll 1
         for (int pass = 0; pass < 2; ++pass) {
             chol_solve_seq<K, kBwdLook>(L, dinv, v, t, gbase, std::make_integer_sequence<int, K>{});
@@ -632,7 +634,7 @@ __device__ __forceinline__ void okrige_solve_block(const HashView& h, const Grid
                 }
             }
 #pragma unroll
-            for (int s = 0; s < kR; ++s) v[s] = ((float)acc[s] * isa) * isx;
+            for (int s = 0; s < kR; ++s) v[s] = (float)acc[s] * isx;  // sa (b - A' x')
         }
 
         // weights and outputs; the weight sum closes in FP64
