@@ -55,13 +55,13 @@ struct Geo {
     static constexpr int SYS = 32 / G;                    // systems per warp
     static constexpr int LEN = G * kR * (kR + 1) / 2;     // register floats of L
     static constexpr int TRI = K * (K + 1) / 2;           // packed lower triangle of A
-    static constexpr int TAB = K + 1;                     // neighbour table length
+    static constexpr int TRIP = (TRI + 3) / 4 * 4;        // the triangle padded to 16 bytes
     // per system: the fixed-point A as a packed lower triangle (row r at
     // r (r + 1) / 2), the three neighbour tables and two column buffers; the
     // stride is = G (mod 32) so that the G-thread groups of a warp spread over
     // the banks
     // two column buffers for the Cholesky broadcasts (16-byte aligned)
-    static constexpr int CB = (TRI + 3 * TAB + 3) / 4 * 4;
+    static constexpr int CB = TRIP + 4 * K;
     static constexpr int RAW = CB + 2 * K;
     static constexpr int SYS_FLOATS = RAW + ((G - RAW % 32) + 32) % 32;
     static constexpr int WARP_FLOATS = SYS * SYS_FLOATS;
@@ -366,9 +366,16 @@ __device__ __forceinline__ void okrige_solve_block(const HashView& h, const Grid
     const int grp = lane / G, t = lane % G, gbase = grp * G;
     float* sysmem = smem + warp * Gm::WARP_FLOATS + grp * Gm::SYS_FLOATS;
     int* Aq = reinterpret_cast<int*>(sysmem);      // packed lower triangle: fixed-point A
-    float* fx = sysmem + Gm::TRI;                   // x of neighbour n minus x of neighbour 0 (cm)
-    float* fy = fx + Gm::TAB;                       // y likewise
-    float* tg = fy + Gm::TAB;                       // Gamma(neighbour of row r, neighbour 0)
+    // one 16-byte record per row r (neighbour r + 1): x and y minus those of
+    // neighbour 0 (cm), Gamma(neighbour r + 1, neighbour 0) in the fixed-point
+    // scale; after assembly the first two hold the row's output terms
+    float* T = sysmem + Gm::TRIP;
+    auto rec = [&](int r) {
+        if constexpr (G >= 4)
+            return *reinterpret_cast<const float4*>(T + 4 * r);
+        else
+            return make_float4(T[4 * r], T[4 * r + 1], T[4 * r + 2], 0.0f);
+    };
     const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << gbase);
 
     for (int round = 0; round < kRounds; ++round) {
@@ -431,8 +438,8 @@ __device__ __forceinline__ void okrige_solve_block(const HashView& h, const Grid
                 }
             }
             const float ox = (float)(rr.x - r0.x), oy = (float)(rr.y - r0.y);
-            fx[r + 1] = ox;
-            fy[r + 1] = oy;
+            T[4 * r] = ox;
+            T[4 * r + 1] = oy;
             zr[s] = __int_as_float(rr.z);
             gr0[s] = real ? gamma_pair_f(p, ox, oy) : 0.0f;
             g0r[s] = real ? gamma_cm(p, rr.x - qx, rr.y - qy, 0.0f) : 0.0f;
@@ -466,7 +473,7 @@ __device__ __forceinline__ void okrige_solve_block(const HashView& h, const Grid
         const int ea = 30 - exp_above(fmaxf(1.0f, 2.0f * gmax));
         const float sa = pow2f(ea);
 #pragma unroll
-        for (int s = 0; s < kR; ++s) tg[G * s + t] = gr0[s] * sa;  // Gamma_r0 in the fixed-point scale
+        for (int s = 0; s < kR; ++s) T[4 * (G * s + t) + 2] = gr0[s] * sa;  // Gamma_r0, fixed-point scale
         const ScaledVgm sv = scaled_vgm(p, sa);
         __syncwarp();
 
@@ -480,12 +487,11 @@ __device__ __forceinline__ void okrige_solve_block(const HashView& h, const Grid
         // group's threads in turn, so no thread idles above its column.
         auto entry_value = [&](auto spherical, int r, int c) {
             constexpr bool kSph = decltype(spherical)::value;
-            const float gc = tg[c];
+            const float4 a = rec(r), b = rec(c);
             // a real row r (r + 1 < ke) implies a real column c < r
-            return (r == c) ? ((c + 1 < ke) ? 2.0f * gc : sa)
-                   : (r + 1 < ke)
-                       ? (tg[r] + gc) - gamma_pair_scaled<kSph>(sv, fx[r + 1] - fx[c + 1], fy[r + 1] - fy[c + 1])
-                       : 0.0f;
+            return (r == c) ? ((c + 1 < ke) ? 2.0f * b.z : sa)
+                   : (r + 1 < ke) ? (a.z + b.z) - gamma_pair_scaled<kSph>(sv, a.x - b.x, a.y - b.y)
+                                  : 0.0f;
         };
         constexpr int kDiag = G * (G + 1) / 2, kDiagSlots = (kDiag + G - 1) / G;
         int dij[kDiagSlots];  // (row, column) in a diagonal block of this thread's slots
@@ -513,20 +519,27 @@ __device__ __forceinline__ void okrige_solve_block(const HashView& h, const Grid
                     if (kDiag % G == 0 || m + 1 < kDiagSlots || t + G * m < kDiag)
                         Aq[tri(G * q + (dij[m] >> 8)) + G * q + (dij[m] & 0xff)] = __float2int_rn(dv[m]);
                 const int c = t + G * q;
-                const float xc = fx[c + 1], yc = fy[c + 1], gcc = tg[c];
+                const float4 cc = rec(c);
+                const float xc = cc.x, yc = cc.y, gcc = cc.z;
                 constexpr int kB = 4;
 #pragma unroll
                 for (int r0 = G * (q + 1); r0 < K; r0 += kB) {
+                    // (K - G (q + 1) need not be a multiple of kB: rows from K on
+                    // are skipped at compile time)
                     float vb[kB];
 #pragma unroll
                     for (int u = 0; u < kB; ++u) {
                         const int r = r0 + u;
-                        vb[u] = (r + 1 < ke)
-                                    ? (tg[r] + gcc) - gamma_pair_scaled<kSph>(sv, fx[r + 1] - xc, fy[r + 1] - yc)
-                                    : 0.0f;
+                        vb[u] = 0.0f;
+                        if (r < K) {
+                            const float4 a = rec(r);
+                            if (r + 1 < ke)
+                                vb[u] = (a.z + gcc) - gamma_pair_scaled<kSph>(sv, a.x - xc, a.y - yc);
+                        }
                     }
 #pragma unroll
-                    for (int u = 0; u < kB; ++u) Aq[tri(r0 + u) + c] = __float2int_rn(vb[u]);
+                    for (int u = 0; u < kB; ++u)
+                        if (r0 + u < K) Aq[tri(r0 + u) + c] = __float2int_rn(vb[u]);
                 }
             }
         };
@@ -547,8 +560,8 @@ __device__ __forceinline__ void okrige_solve_block(const HashView& h, const Grid
             b[s] = (r + 1 < ke) ? (gr0[s] + g00) - g0r[s] : 0.0f;
             // the tables are free after assembly: keep the row's output terms
             // there rather than in registers through the solve
-            fx[r + 1] = zr[s] - z0;
-            fy[r + 1] = g0r[s] - gr0[s];
+            T[4 * r] = zr[s] - z0;
+            T[4 * r + 1] = g0r[s] - gr0[s];
 #pragma unroll
             for (int c = 0; c < G * (s + 1); ++c) {
                 const int q = Aq[c <= r ? tri(r) + c : 0];
@@ -644,8 +657,8 @@ __device__ __forceinline__ void okrige_solve_block(const HashView& h, const Grid
             const bool row = G * s + t + 1 < ke;
             const float lam = row ? x[s] : 0.0f;
             ps += lam;
-            pz = fmaf(lam, fx[G * s + t + 1], pz);  // z_a - z_0
-            pv = fmaf(lam, fy[G * s + t + 1], pv);  // gamma_0a - Gamma_a0
+            pz = fmaf(lam, T[4 * (G * s + t)], pz);      // z_a - z_0
+            pv = fmaf(lam, T[4 * (G * s + t) + 1], pv);  // gamma_0a - Gamma_a0
         }
         double wsum = (double)ps;
 #pragma unroll
