@@ -612,10 +612,10 @@ def bench_ours(args):
     out_h = [torch.empty(m, pin_memory=True) for _ in range(3)]
 
     def e2e_step():
+        # the grids go to pinned host memory chunk by chunk, each chunk's copy
+        # overlapping the later chunks' kernels (bg_interp_idw_okrige_host)
         s = bg.soundings_upload(ctx, xh, yh, zh, stream=stream)
-        bg.interp_idw_okrige(s, grid, IDW_K, IDW_P, OK_K, vgm, d_idw, d_ok, v_ok)
-        for h, d in zip(out_h, (d_idw, d_ok, v_ok)):
-            h.copy_(d, non_blocking=True)
+        bg.interp_idw_okrige_host(s, grid, IDW_K, IDW_P, OK_K, vgm, d_idw, d_ok, v_ok, *out_h)
         bg.soundings_destroy(s)
 
     e2e_step()

@@ -167,6 +167,25 @@ bg_status bg_interp_idw_okrige(bg_soundings_t s, bg_grid_t grid, int k_idw, floa
                                int k_okrige, const bg_variogram* v, float* idw_out,
                                float* depth_out, float* var_out, void* cuda_stream);
 
+/* bg_interp_idw_okrige with the three grids also delivered to host memory:
+ * each row chunk's outputs are copied to idw_host / depth_host / var_host on
+ * the context's copy stream as soon as that chunk's kernels have finished,
+ * so the download overlaps the later chunks' work instead of following the
+ * whole call. The device outputs are filled as by bg_interp_idw_okrige
+ * (bitwise the same values).
+ *   idw_out, depth_out, var_out, k_idw, power, k_okrige, v: as for
+ *     bg_interp_idw_okrige.
+ *   idw_host, depth_host, var_host: host, nx*ny float32 each, or NULL (that
+ *     grid is not copied); var_host needs var_out. Page-locked memory
+ *     (cudaMallocHost, cudaHostRegister) overlaps; pageable memory gives the
+ *     same result without the overlap. The caller owns them.
+ * Asynchronous on cuda_stream: later work on cuda_stream waits for the last
+ * copy, so the host arrays are complete once cuda_stream is synchronized. */
+bg_status bg_interp_idw_okrige_host(bg_soundings_t s, bg_grid_t grid, int k_idw, float power,
+                                    int k_okrige, const bg_variogram* v, float* idw_out,
+                                    float* depth_out, float* var_out, float* idw_host,
+                                    float* depth_host, float* var_host, void* cuda_stream);
+
 /* The same two methods at a list of query points instead of grid nodes: the
  * paper's hole filling interpolates the missing entries of a grid (Sec. IV,
  * Grid B) and its runtime tests interpolate batches of generated points

@@ -28,7 +28,7 @@ __all__ = [
     "version", "launch_count", "profile_enable", "profile_read", "ctx_create", "ctx_destroy",
     "ctx_device_bytes", "grid_create", "grid_destroy",
     "soundings_upload", "soundings_info", "soundings_destroy", "interp_idw", "interp_okrige",
-    "interp_idw_okrige", "interp_idw_points", "interp_okrige_points", "BILINEAR", "CATMULL_ROM", "resample_points",
+    "interp_idw_okrige", "interp_idw_okrige_host", "interp_idw_points", "interp_okrige_points", "BILINEAR", "CATMULL_ROM", "resample_points",
     "resample_grid",
     "variogram", "interp_idw_noalloc", "submit", "poll", "wait", "cancel", "serve_stats",
     "serve_shutdown", "Request", "Result", "Batch", "batch_create", "batch_run", "batch_tune",
@@ -192,6 +192,30 @@ def interp_idw_okrige(s, grid, k_idw: int, power: float, k_okrige: int, vgm: Var
     check(_lib().bg_interp_idw_okrige(s, grid, k_idw, power, k_okrige, ctypes.byref(vgm),
                                       _ptr(idw_out), _ptr(depth_out), _ptr(var_out),
                                       _stream(stream, depth_out)), "bg_interp_idw_okrige")
+
+
+def interp_idw_okrige_host(s, grid, k_idw: int, power: float, k_okrige: int, vgm: Variogram,
+                           idw_out, depth_out, var_out=None, idw_host=None, depth_host=None,
+                           var_host=None, stream=None) -> None:
+    """interp_idw_okrige that also copies each row chunk's grids to host arrays
+    (CPU tensors, pinned for overlap) while the later chunks compute; the host
+    arrays are complete once `stream` is synchronized."""
+    for t in (idw_out, depth_out):
+        _check_dtype(t, "float32")
+    m = int(depth_out.shape[0])
+    for t in (var_out, idw_host, depth_host, var_host):
+        if t is not None:
+            _check_dtype(t, "float32")
+    for t in (idw_host, depth_host, var_host):
+        if t is not None:
+            if _is_cuda(t):
+                raise ValueError("host destinations must be host tensors or arrays")
+            if int(t.shape[0]) != m:
+                raise ValueError("host destinations need nx*ny entries")
+    check(_lib().bg_interp_idw_okrige_host(s, grid, k_idw, power, k_okrige, ctypes.byref(vgm),
+                                           _ptr(idw_out), _ptr(depth_out), _ptr(var_out),
+                                           _ptr(idw_host), _ptr(depth_host), _ptr(var_host),
+                                           _stream(stream, depth_out)), "bg_interp_idw_okrige_host")
 
 
 def _check_points(qx_cm, qy_cm, depth_out):

@@ -89,6 +89,8 @@ _SIGNATURES = {
                          ctypes.c_int),
     "bg_interp_idw_okrige": ([P, P, ctypes.c_int, ctypes.c_float, ctypes.c_int,
                               ctypes.POINTER(Variogram), P, P, P, P], ctypes.c_int),
+    "bg_interp_idw_okrige_host": ([P, P, ctypes.c_int, ctypes.c_float, ctypes.c_int,
+                                   ctypes.POINTER(Variogram), P, P, P, P, P, P, P], ctypes.c_int),
     "bg_interp_idw_points": ([P, P, P, ctypes.c_int64, ctypes.c_int, ctypes.c_float, P, P, P],
                              ctypes.c_int),
     "bg_interp_okrige_points": ([P, P, P, ctypes.c_int64, ctypes.c_int, ctypes.POINTER(Variogram),

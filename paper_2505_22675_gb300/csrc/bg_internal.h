@@ -69,6 +69,18 @@ struct IdwFuse {
     int k = 0;
 };
 
+// Host destinations of a grid call's outputs (page-locked; NULL: not copied):
+// the rows of each chunk are copied on the stream cs once the chunk's kernels
+// have finished on the caller's stream, so the copies overlap the next
+// chunk's work; ev orders the two streams.
+struct HostOut {
+    float* idw = nullptr;
+    float* depth = nullptr;
+    float* var = nullptr;
+    cudaStream_t cs = nullptr;
+    cudaEvent_t ev = nullptr;
+};
+
 // Query points: m device coordinates (cm) in two arrays.
 struct PointsView {
     const int32_t* x;
@@ -117,6 +129,7 @@ struct bg_ctx_s {
     int32_t* h_pinned = nullptr;       // pinned host scratch for the bbox read-back
     int n_grids = 0, n_soundings = 0;
     bg::Server* server = nullptr;      // serving state (created by the first bg_submit)
+    cudaStream_t copy_stream = nullptr;  // device-to-host copies that overlap later kernels
 };
 
 struct bg_grid_s {
@@ -210,9 +223,10 @@ bg_status launch_idw_with_flag(const bg_soundings_s* s, const GridView& g, int k
 bg_status launch_idw(const bg_soundings_s* s, const GridView& g, int k, float power,
                      float* depth, int32_t* nbr, cudaStream_t st);
 // fz: NULL, or an IDW to write in the same pass (fz->k <= k)
+// ho: NULL, or host destinations that each row chunk's outputs are copied to
 bg_status launch_okrige(const bg_soundings_s* s, const GridView& g, int k, const OkParams& p,
                         float* depth, float* var, int32_t* nbr, cudaStream_t st,
-                        const IdwFuse* fz = nullptr);
+                        const IdwFuse* fz = nullptr, const HostOut* ho = nullptr);
 
 // Gridded input (bilinear / Catmull-Rom) at query points or output-grid nodes;
 // no allocation.

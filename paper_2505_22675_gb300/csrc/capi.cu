@@ -179,7 +179,9 @@ bg_status bg_ctx_create(int device, size_t hbm_budget_bytes, bg_ctx_t* out) {
         e = cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &keep);
     }
     if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_pinned, 64 * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
+        if (c->h_pinned) cudaFreeHost(c->h_pinned);
         if (c->pool) cudaMemPoolDestroy(c->pool);
         delete c;
         return cuda_fail(e, "context set-up");
@@ -237,6 +239,7 @@ bg_status bg_ctx_destroy(bg_ctx_t ctx) {
         cudaEventDestroy(e.b);
     }
     for (auto e : ctx->prof.spare) cudaEventDestroy(e);
+    cudaStreamDestroy(ctx->copy_stream);
     cudaFreeHost(ctx->h_pinned);
     cudaMemPoolDestroy(ctx->pool);
     delete ctx;
@@ -388,6 +391,37 @@ bg_status bg_interp_idw_okrige(bg_soundings_t s, bg_grid_t grid, int k_idw, floa
     fz.k = k_idw;
     return launch_okrige(s, grid->g, k_okrige, p, depth_out, var_out, nullptr,
                          (cudaStream_t)cuda_stream, &fz);
+}
+
+bg_status bg_interp_idw_okrige_host(bg_soundings_t s, bg_grid_t grid, int k_idw, float power,
+                                    int k_okrige, const bg_variogram* v, float* idw_out,
+                                    float* depth_out, float* var_out, float* idw_host,
+                                    float* depth_host, float* var_host, void* cuda_stream) {
+    bg::NvtxRange nvtx("bg_interp_idw_okrige_host");
+    bg_status rc = check_interp(s, grid, k_okrige, depth_out);
+    if (rc != BG_OK) return rc;
+    BG_REQUIRE(idw_out, "idw_out is NULL");
+    BG_REQUIRE(!var_host || var_out, "var_host needs var_out");
+    BG_REQUIRE(k_idw >= 1 && k_idw <= k_okrige, "k_idw must be in [1, k_okrige]");
+    BG_REQUIRE(finite_pos(power), "power must be finite and > 0");
+    OkParams p;
+    if (!okrige_params(v, &p)) return BG_ERR_INVALID_ARG;
+    DeviceGuard dg(s->ctx->device);
+    if (!dg.ok) return cuda_fail(cudaGetLastError(), "cudaSetDevice");
+    IdwFuse fz;
+    fz.out = idw_out;
+    fz.power = power;
+    fz.k = k_idw;
+    HostOut ho;
+    ho.idw = idw_host;
+    ho.depth = depth_host;
+    ho.var = var_host;
+    ho.cs = s->ctx->copy_stream;
+    BG_CUDA(cudaEventCreateWithFlags(&ho.ev, cudaEventDisableTiming));
+    rc = launch_okrige(s, grid->g, k_okrige, p, depth_out, var_out, nullptr,
+                       (cudaStream_t)cuda_stream, &fz, &ho);
+    cudaEventDestroy(ho.ev);  // released once its last record completes
+    return rc;
 }
 
 static bg_status check_points(bg_soundings_t s, const int32_t* qx, const int32_t* qy, int64_t m,

@@ -59,9 +59,26 @@ __global__ void __launch_bounds__(kSolveWarps * 32, kSolveBlocksPerSM) k_okrige_
                                        nullptr, nullptr, fz);
 }
 
+// Copy rows [off, off + n) of the outputs to their host destinations on
+// ho->cs, after the work enqueued so far on st.
+bg_status copy_rows_to_host(const HostOut* ho, int64_t off, int64_t n, const float* idw,
+                            const float* depth, const float* var, cudaStream_t st) {
+    cudaError_t e = cudaEventRecord(ho->ev, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ho->cs, ho->ev, 0);
+    const size_t bytes = (size_t)n * sizeof(float);
+    if (e == cudaSuccess && ho->idw && idw)
+        e = cudaMemcpyAsync(ho->idw + off, idw + off, bytes, cudaMemcpyDeviceToHost, ho->cs);
+    if (e == cudaSuccess && ho->depth)
+        e = cudaMemcpyAsync(ho->depth + off, depth + off, bytes, cudaMemcpyDeviceToHost, ho->cs);
+    if (e == cudaSuccess && ho->var && var)
+        e = cudaMemcpyAsync(ho->var + off, var + off, bytes, cudaMemcpyDeviceToHost, ho->cs);
+    return e == cudaSuccess ? BG_OK : cuda_fail(e, "device-to-host copy");
+}
+
 template <int K>
 bg_status launch_k(const HashView& h, const GridView& g, int k, const OkParams& p, float* depth,
-                   float* var, int32_t* nbr, bg_ctx_s* ctx, cudaStream_t st, const IdwFuse* fz) {
+                   float* var, int32_t* nbr, bg_ctx_s* ctx, cudaStream_t st, const IdwFuse* fz,
+                   const HostOut* ho) {
     using Gm = Geo<K>;
     // grid rows per chunk: the id buffer stays near 1 GiB unless the caller
     // passed nbr_out, which then holds all ids
@@ -114,6 +131,15 @@ bg_status launch_k(const HashView& h, const GridView& g, int k, const OkParams& 
             rc = cuda_fail(e, "kriging launch");
             break;
         }
+        if (ho) {
+            rc = copy_rows_to_host(ho, j0 * g.nx, nodes, fz ? fz->out : nullptr, depth, var, st);
+            if (rc != BG_OK) break;
+        }
+    }
+    if (ho && rc == BG_OK) {  // later work on st waits for the last copy
+        cudaError_t e = cudaEventRecord(ho->ev, ho->cs);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ho->ev, 0);
+        if (e != cudaSuccess) rc = cuda_fail(e, "copy-stream join");
     }
     dfree(ctx, scratch, flag_bytes + id_bytes, st);
     return rc;
@@ -229,22 +255,28 @@ bg_status launch_okrige_points(const bg_soundings_s* s, const PointsView& q, int
 
 bg_status launch_okrige(const bg_soundings_s* s, const GridView& g, int k, const OkParams& p,
                         float* depth, float* var, int32_t* nbr, cudaStream_t st,
-                        const IdwFuse* fz) {
+                        const IdwFuse* fz, const HostOut* ho) {
     HashView h = s->h;
     const int K = k <= 4 ? 4 : k <= 8 ? 8 : k <= 16 ? 16 : 32;
     if (fz && K != 32) {
         // smaller systems run 2 or 4 threads each: the IDW takes its own pass
         // (the same depths: idw_from sums in the same fixed order)
-        const bg_status rc = launch_idw(s, g, fz->k, fz->power, fz->out, nullptr, st);
+        bg_status rc = launch_idw(s, g, fz->k, fz->power, fz->out, nullptr, st);
         if (rc != BG_OK) return rc;
+        if (ho && ho->idw) {  // the whole IDW grid is done: copy it now
+            HostOut only_idw = *ho;
+            only_idw.depth = only_idw.var = nullptr;
+            rc = copy_rows_to_host(&only_idw, 0, (int64_t)g.nx * g.ny, fz->out, nullptr, nullptr, st);
+            if (rc != BG_OK) return rc;
+        }
         fz = nullptr;
     }
     h.r0 = start_halfwidth(s, K);
     switch (K) {
-        case 4: return launch_k<4>(h, g, k, p, depth, var, nbr, s->ctx, st, fz);
-        case 8: return launch_k<8>(h, g, k, p, depth, var, nbr, s->ctx, st, fz);
-        case 16: return launch_k<16>(h, g, k, p, depth, var, nbr, s->ctx, st, fz);
-        default: return launch_k<32>(h, g, k, p, depth, var, nbr, s->ctx, st, fz);
+        case 4: return launch_k<4>(h, g, k, p, depth, var, nbr, s->ctx, st, fz, ho);
+        case 8: return launch_k<8>(h, g, k, p, depth, var, nbr, s->ctx, st, fz, ho);
+        case 16: return launch_k<16>(h, g, k, p, depth, var, nbr, s->ctx, st, fz, ho);
+        default: return launch_k<32>(h, g, k, p, depth, var, nbr, s->ctx, st, fz, ho);
     }
 }
 

@@ -67,7 +67,16 @@ def swath_run():
     out["fused_same"] = bool(torch.equal(fi.view(torch.int32), di.view(torch.int32))
                              and torch.equal(fd.view(torch.int32), d.view(torch.int32))
                              and torch.equal(fv.view(torch.int32), v.view(torch.int32)))
-    del d, v, d2, v2, fi, fd, fv, di
+    # the same pass delivering the grids to pinned host memory chunk by chunk
+    # (copies overlapped with the later chunks) gives bitwise the device grids
+    hi, hd, hv = (torch.full((g.m,), -7.0, pin_memory=True) for _ in range(3))
+    gi, gd, gv = (torch.empty(g.m, device=dev) for _ in range(3))
+    bg.interp_idw_okrige_host(s, grid, 16, 2.0, 32, bg.variogram(0, 0.25, 100.0, 50.0),
+                              gi, gd, gv, hi, hd, hv)
+    torch.cuda.current_stream().synchronize()
+    out["host_same"] = bool(all(torch.equal(h.view(torch.int32), a.cpu().view(torch.int32))
+                                for h, a in ((hi, fi), (hd, fd), (hv, fv))))
+    del d, v, d2, v2, fi, fd, fv, di, gi, gd, gv, hi, hd, hv
     torch.cuda.synchronize()
     bg.soundings_destroy(s)
     bg.grid_destroy(grid)
@@ -102,3 +111,7 @@ def test_swath_okrige_row_chunks_match_one_pass(swath_run):
 
 def test_swath_fused_pass_matches_separate_calls(swath_run):
     assert swath_run[3]["fused_same"]
+
+
+def test_swath_grids_delivered_to_host_match_device(swath_run):
+    assert swath_run[3]["host_same"]

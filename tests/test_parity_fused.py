@@ -105,3 +105,44 @@ def test_fused_rejects_k_idw_above_k_okrige():
         bg.grid_destroy(grid)
     finally:
         bg.ctx_destroy(ctx)
+
+
+@pytest.mark.parametrize("k_idw,k_ok,with_var", [(16, 32, True), (8, 16, True), (4, 32, False)])
+def test_grids_delivered_to_host(k_idw, k_ok, with_var):
+    """bg_interp_idw_okrige_host: the host arrays (pinned or pageable) hold
+    bitwise the device grids once the stream is synchronized; K = 16 takes the
+    separate IDW pass and copies the whole IDW grid first."""
+    import torch
+
+    import paper_2505_22675_gb300 as bg
+    w = synth.tile(seed=57, n=6000, side_cm=30_000, cell_cm=200)
+    g = w.grid
+    dev = torch.device("cuda:0")
+    ctx = bg.ctx_create(0)
+    try:
+        grid = bg.grid_create(ctx, g.x0_cm, g.y0_cm, g.cell_cm, g.nx, g.ny)
+        s = bg.soundings_upload(ctx, *(torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+                                       for a in (w.x_cm, w.y_cm, w.z_m)))
+        v = bg.variogram(*SPH)
+        for pinned in (True, False):
+            dv = [torch.empty(g.m, device=dev) for _ in range(3)]
+            hv = [torch.full((g.m,), -7.0, pin_memory=pinned) for _ in range(3)]
+            bg.interp_idw_okrige_host(s, grid, k_idw, 2.0, k_ok, v, dv[0], dv[1],
+                                      dv[2] if with_var else None, hv[0], hv[1],
+                                      hv[2] if with_var else None)
+            torch.cuda.current_stream().synchronize()
+            for i in range(3 if with_var else 2):
+                assert _bitwise(hv[i].numpy(), dv[i].cpu().numpy())
+            if not with_var:
+                assert (hv[2].numpy() == -7.0).all()
+            ref = [torch.empty(g.m, device=dev) for _ in range(3)]
+            bg.interp_idw_okrige(s, grid, k_idw, 2.0, k_ok, v, *ref)
+            torch.cuda.synchronize()
+            assert _bitwise(hv[1].numpy(), ref[1].cpu().numpy())
+        with pytest.raises(bg.BGError):  # var_host without var_out
+            bg.interp_idw_okrige_host(s, grid, k_idw, 2.0, k_ok, v, dv[0], dv[1], None,
+                                      hv[0], hv[1], hv[2])
+        bg.soundings_destroy(s)
+        bg.grid_destroy(grid)
+    finally:
+        bg.ctx_destroy(ctx)
