@@ -29,9 +29,19 @@ __global__ void __launch_bounds__(64) k_knn_ids(HashView h, GridView g, int k, i
         return;
     }
     const uint64_t mask = (1ull << h.idx_bits) - 1;
+    // k == K (a multiple of 4) puts every node's ids on a 16-byte boundary when
+    // the buffer is aligned: four ids per store instead of one
+    const bool vec = k == K && K % 4 == 0 && (reinterpret_cast<uintptr_t>(ids) & 15) == 0;
     knn_strip<64>(h, g, K, o.i, o.j, hp, flag, [&](int i, int cnt) {
         int32_t* out = base + (int64_t)i * k;
-        for (int q = 0; q < k; ++q) out[q] = q < cnt ? (int)(hp[q * 64] & mask) : -1;
+        auto id = [&](int q) { return q < cnt ? (int)(hp[q * 64] & mask) : -1; };
+        if (vec) {
+#pragma unroll
+            for (int q = 0; q < K; q += 4)
+                *reinterpret_cast<int4*>(out + q) = make_int4(id(q), id(q + 1), id(q + 2), id(q + 3));
+        } else {
+            for (int q = 0; q < k; ++q) out[q] = id(q);
+        }
     });
 }
 
