@@ -310,9 +310,7 @@ __global__ void __launch_bounds__(kKnnThreads) k_batch_knn(
                     ii = (int)(key & mask);
                 });
             } else {
-                int32_t* o = d.ids + node * k;
-                for (int i = 0; i < k; ++i)
-                    o[i] = i < keff ? (int)(hp[i * kKnnThreads] & mask) : -1;
+                emit_ids<kKnnThreads>(d.ids + node * k, hp, k, keff, mask);
             }
         }
     }

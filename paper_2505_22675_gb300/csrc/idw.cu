@@ -37,10 +37,7 @@ __global__ void __launch_bounds__(128) k_idw(HashView h, GridView g, int k, floa
             dd = key >> bits;
             ii = (int)(key & mask);
         });
-        if (nbr) {
-            int32_t* out = nbr + (row + i) * k;
-            for (int q = 0; q < k; ++q) out[q] = q < keff ? (int)(hp[q * 128] & mask) : -1;
-        }
+        if (nbr) emit_ids<128>(nbr + (row + i) * k, hp, k, keff, mask);
     });
 }
 
@@ -107,10 +104,7 @@ __global__ void __launch_bounds__(128) k_idw_pts(HashView h, PointsView q, int k
             dd = key >> bits;
             ii = (int)(key & mask);
         });
-        if (nbr) {
-            int32_t* out = nbr + p * k;
-            for (int i = 0; i < k; ++i) out[i] = i < keff ? (int)(hp[i * 128] & mask) : -1;
-        }
+        if (nbr) emit_ids<128>(nbr + p * k, hp, k, keff, mask);
     });
 }
 

@@ -379,6 +379,22 @@ __device__ __forceinline__ int knn_scan_heap(const HashView& h, int qx, int qy, 
     return knn_scan_heap_rt<S>(h, qx, qy, b, hp, K);
 }
 
+// The first k ids of a thread's sorted heap (stride S) to out, -1 from cnt
+// on: four ids per 16-byte store when k is a multiple of 4 and out is
+// 16-byte aligned (a node's ids then never straddle a boundary), else one by
+// one.
+template <int S>
+__device__ __forceinline__ void emit_ids(int32_t* __restrict__ out, const uint64_t* hp, int k,
+                                         int cnt, uint64_t mask) {
+    auto id = [&](int q) { return q < cnt ? (int)(hp[q * S] & mask) : -1; };
+    if ((k & 3) == 0 && (reinterpret_cast<uintptr_t>(out) & 15) == 0) {
+        for (int q = 0; q < k; q += 4)
+            *reinterpret_cast<int4*>(out + q) = make_int4(id(q), id(q + 1), id(q + 2), id(q + 3));
+    } else {
+        for (int q = 0; q < k; ++q) out[q] = id(q);
+    }
+}
+
 // Grid node (i, j) owned by this thread inside the 16 x 8 node patch (px, py).
 // Each warp covers 8 x 4 nodes, so a warp's nodes are spatially compact.
 struct NodeIdx {

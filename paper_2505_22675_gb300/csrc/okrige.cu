@@ -173,8 +173,7 @@ __global__ void __launch_bounds__(128) k_knn_ids_pts(HashView h, PointsView q, i
     }
     const uint64_t mask = (1ull << h.idx_bits) - 1;
     knn_chain<128>(h, q.x, q.y, a, p1, K, hp, flag, [&](int64_t p, int cnt) {
-        int32_t* out = ids + (p - p0) * k;
-        for (int i = 0; i < k; ++i) out[i] = i < cnt ? (int)(hp[i * 128] & mask) : -1;
+        emit_ids<128>(ids + (p - p0) * k, hp, k, cnt, mask);
     });
 }
 
