@@ -288,7 +288,7 @@ __device__ __forceinline__ void heap_build(uint64_t* hp, int n) {
 
 // Phase 2 with the heap. On return hp[0 .. keff) holds the neighbours' packed
 // keys in ascending order; returns keff (<= kc). Requires packed_fits(tau0).
-template <int S>
+template <int S, bool kSort = true>
 __device__ __forceinline__ int knn_scan_heap_rt(const HashView& h, int qx, int qy, const Bound& b,
                                                 uint64_t* hp, int kc) {
     const int bits = h.idx_bits;
@@ -363,8 +363,9 @@ __device__ __forceinline__ int knn_scan_heap_rt(const HashView& h, int qx, int q
         if (p < e) take(__ldg(h.rec + p));
         tau = min(tau, (int64_t)(root >> bits));
     }
-    // heapsort into ascending order
     if (cnt < kc) heap_build<S>(hp, cnt);
+    if constexpr (!kSort) return cnt;  // left a max-heap (the caller drains it)
+    // heapsort into ascending order
     for (int e = cnt - 1; e > 0; --e) {
         const uint64_t v = hp[e * S];
         hp[e * S] = hp[0];
@@ -392,6 +393,25 @@ __device__ __forceinline__ void emit_ids(int32_t* __restrict__ out, const uint64
             *reinterpret_cast<int4*>(out + q) = make_int4(id(q), id(q + 1), id(q + 2), id(q + 3));
     } else {
         for (int q = 0; q < k; ++q) out[q] = id(q);
+    }
+}
+
+// Drain a full max-heap of K keys (stride S) into the ids of ascending
+// order: each extraction's maximum is the id of the next slot from the end,
+// written four at a time with one 16-byte store (out 16-byte aligned), so
+// the heap is never written back in sorted order and read again.
+template <int K, int S>
+__device__ __forceinline__ void drain_ids(int32_t* __restrict__ out, uint64_t* hp, uint64_t mask) {
+    static_assert(K % 4 == 0, "whole 16-byte groups");
+    for (int m = K / 4 - 1; m >= 0; --m) {
+        int v[4];
+#pragma unroll
+        for (int u = 3; u >= 0; --u) {
+            const int e = 4 * m + u;  // heap size before this extraction is e + 1
+            v[u] = (int)(hp[0] & mask);
+            if (e > 0) heap_sift_down<S>(hp, 0, e, hp[e * S]);
+        }
+        *reinterpret_cast<int4*>(out + 4 * m) = make_int4(v[0], v[1], v[2], v[3]);
     }
 }
 
@@ -423,7 +443,7 @@ __device__ __forceinline__ NodeIdx strip_origin(int px, int py, int warp, int la
 // shared-memory heap hp (stride S). emit(i, cnt) runs after each node with its
 // keys sorted ascending in hp[0 .. cnt); a node whose table bound does not
 // fit the packed key is left to the wide pass (*flag = 1).
-template <int S, class Emit>
+template <int S, class Emit, bool kSort = true>
 __device__ __forceinline__ void knn_strip(const HashView& h, const GridView& g, int kc, int i0,
                                           int j, uint64_t* hp, int* flag, Emit emit) {
     const int qy = g.y0 + j * g.cell + g.cell / 2;
@@ -449,8 +469,9 @@ __device__ __forceinline__ void knn_strip(const HashView& h, const GridView& g, 
                 continue;
             }
         }
-        const int cnt = knn_scan_heap_rt<S>(h, qx, qy, b, hp, kc);
-        prev = cnt == kc ? (int64_t)(hp[(kc - 1) * S] >> h.idx_bits) : -1;
+        const int cnt = knn_scan_heap_rt<S, kSort>(h, qx, qy, b, hp, kc);
+        // the K-th key: the last one when sorted, the root of the heap when not
+        prev = cnt == kc ? (int64_t)(hp[(kSort ? kc - 1 : 0) * S] >> h.idx_bits) : -1;
         emit(i, cnt);
     }
 }

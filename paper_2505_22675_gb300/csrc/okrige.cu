@@ -30,19 +30,23 @@ __global__ void __launch_bounds__(64) k_knn_ids(HashView h, GridView g, int k, i
     }
     const uint64_t mask = (1ull << h.idx_bits) - 1;
     // k == K (a multiple of 4) puts every node's ids on a 16-byte boundary when
-    // the buffer is aligned: four ids per store instead of one
+    // the buffer is aligned: a full heap is then drained straight into them,
+    // four ids per store; otherwise it is sorted in place and copied out
     const bool vec = k == K && K % 4 == 0 && (reinterpret_cast<uintptr_t>(ids) & 15) == 0;
-    knn_strip<64>(h, g, K, o.i, o.j, hp, flag, [&](int i, int cnt) {
+    auto emit = [&](int i, int cnt) {
         int32_t* out = base + (int64_t)i * k;
-        auto id = [&](int q) { return q < cnt ? (int)(hp[q * 64] & mask) : -1; };
-        if (vec) {
-#pragma unroll
-            for (int q = 0; q < K; q += 4)
-                *reinterpret_cast<int4*>(out + q) = make_int4(id(q), id(q + 1), id(q + 2), id(q + 3));
-        } else {
-            for (int q = 0; q < k; ++q) out[q] = id(q);
+        if (vec && cnt == K) {
+            drain_ids<K, 64>(out, hp, mask);
+            return;
         }
-    });
+        for (int e = cnt - 1; e > 0; --e) {  // heapsort of a partial heap
+            const uint64_t v = hp[e * 64];
+            hp[e * 64] = hp[0];
+            heap_sift_down<64>(hp, 0, e, v);
+        }
+        emit_ids<64>(out, hp, k, cnt, mask);
+    };
+    knn_strip<64, decltype(emit), false>(h, g, K, o.i, o.j, hp, flag, emit);
 }
 
 template <int K>
