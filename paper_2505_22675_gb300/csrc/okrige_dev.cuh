@@ -57,10 +57,9 @@ struct Geo {
     static constexpr int TRI = K * (K + 1) / 2;           // packed lower triangle of A
     static constexpr int TRIP = (TRI + 3) / 4 * 4;        // the triangle padded to 16 bytes
     // per system: the fixed-point A as a packed lower triangle (row r at
-    // r (r + 1) / 2), the three neighbour tables and two column buffers; the
-    // stride is = G (mod 32) so that the G-thread groups of a warp spread over
-    // the banks
-    // two column buffers for the Cholesky broadcasts (16-byte aligned)
+    // r (r + 1) / 2), one 16-byte record per row, and two column buffers for
+    // the Cholesky broadcasts (16-byte aligned); the stride is = G (mod 32) so
+    // that the G-thread groups of a warp spread over the banks
     static constexpr int CB = TRIP + 4 * K;
     static constexpr int RAW = CB + 2 * K;
     static constexpr int SYS_FLOATS = RAW + ((G - RAW % 32) + 32) % 32;
@@ -478,8 +477,9 @@ __device__ __forceinline__ void okrige_solve_block(const HashView& h, const Grid
         __syncwarp();
 
         // assemble the lower triangle once per entry, straight into fixed
-        // point. Every term is in the fixed-point scale already (tg and the
-        // scaled variogram), so an entry is one rounding to integer. The
+        // point. Every term is in the fixed-point scale already (the records'
+        // Gamma_r0 and the scaled variogram), so an entry is one rounding to
+        // integer. The
         // triangle splits into G x G blocks: below the diagonal blocks,
         // thread t owns the columns c = t + G q and the group walks the rows
         // in step (a row's entries land in consecutive banks); the
