@@ -175,3 +175,38 @@ def test_small_swath_k32_sampled_nodes_including_gaps():
                                                    "range_m": 50.0})
     assert np.array_equal(nb[sel], ridx)
     assert_okrige(d[sel], v[sel], rd, rv, SPH["nugget"])
+
+
+@pytest.mark.parametrize("k", [32, 16])
+def test_neighbour_output_at_an_unaligned_address(k):
+    """nbr_out 4 bytes past a 16-byte boundary: the k-NN kernels store ids four
+    at a time only into aligned buffers, so here they fall back to one at a
+    time; ids and grids equal those of an aligned buffer (IDW and kriging)."""
+    import torch
+
+    import paper_2505_22675_gb300 as bg
+    w = synth.tile(seed=8, n=5000, side_cm=25_000, cell_cm=250)
+    lib = Lib(w.x_cm, w.y_cm, w.z_m, w.grid)
+    try:
+        m = w.grid.nx * w.grid.ny
+        d_al, v_al, nb_al = lib.okrige(k)
+        i_al, ib_al = lib.idw(k, 2.0)
+        raw = torch.full((m * k + 4,), -9, dtype=torch.int32, device=lib.dev)
+        nb = raw[1:1 + m * k]
+        assert nb.data_ptr() % 16 == 4
+        d = torch.empty(m, device=lib.dev)
+        v = torch.empty(m, device=lib.dev)
+        bg.interp_okrige(lib.s, lib.grid, k, bg.variogram(0, 0.25, 100.0, 50.0), d, v, nb)
+        torch.cuda.synchronize()
+        assert np.array_equal(nb.cpu().numpy().reshape(m, k), nb_al)
+        assert np.array_equal(d.cpu().numpy().view(np.uint32), d_al.view(np.uint32))
+        assert np.array_equal(v.cpu().numpy().view(np.uint32), v_al.view(np.uint32))
+        assert raw[0].item() == -9 and raw[1 + m * k].item() == -9
+        raw.fill_(-9)
+        bg.interp_idw(lib.s, lib.grid, k, 2.0, d, nb)
+        torch.cuda.synchronize()
+        assert np.array_equal(nb.cpu().numpy().reshape(m, k), ib_al)
+        assert np.array_equal(d.cpu().numpy().view(np.uint32), i_al.view(np.uint32))
+        assert raw[0].item() == -9 and raw[1 + m * k].item() == -9
+    finally:
+        lib.close()
