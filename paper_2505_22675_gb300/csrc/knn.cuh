@@ -364,12 +364,12 @@ __device__ __forceinline__ int knn_scan_heap_rt(const HashView& h, int qx, int q
         tau = min(tau, (int64_t)(root >> bits));
     }
     if (cnt < kc) heap_build<S>(hp, cnt);
-    if constexpr (!kSort) return cnt;  // left a max-heap (the caller drains it)
-    // heapsort into ascending order
-    for (int e = cnt - 1; e > 0; --e) {
-        const uint64_t v = hp[e * S];
-        hp[e * S] = hp[0];
-        heap_sift_down<S>(hp, 0, e, v);
+    if constexpr (kSort) {  // heapsort into ascending order (else the caller drains the max-heap)
+        for (int e = cnt - 1; e > 0; --e) {
+            const uint64_t v = hp[e * S];
+            hp[e * S] = hp[0];
+            heap_sift_down<S>(hp, 0, e, v);
+        }
     }
     return cnt;
 }

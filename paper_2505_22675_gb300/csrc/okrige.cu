@@ -63,14 +63,15 @@ __global__ void __launch_bounds__(128) k_knn_ids_wide(HashView h, GridView g, in
                               nullptr);
 }
 
+// dynamic shared memory: kGridSolveWarps * Geo<K>::WARP_FLOATS floats
 template <int K, bool kIdw>
-__global__ void __launch_bounds__(kSolveWarps * 32, kSolveBlocksPerSM) k_okrige_solve(
+__global__ void __launch_bounds__(kGridSolveWarps * 32, kGridSolveBlocksPerSM) k_okrige_solve(
     HashView h, GridView g, int k, OkParams p, int64_t node0, int64_t nodes,
     const int32_t* __restrict__ ids, float* __restrict__ depth, float* __restrict__ var,
     IdwFuse fz) {
-    __shared__ __align__(16) float smem[kSolveWarps * Geo<K>::WARP_FLOATS];
-    okrige_solve_block<K, false, kIdw>(h, g, k, p, node0, nodes, ids, depth, var, blockIdx.x, smem,
-                                       nullptr, nullptr, fz);
+    extern __shared__ __align__(16) float smem[];
+    okrige_solve_block<K, false, kIdw, kGridSolveWarps>(h, g, k, p, node0, nodes, ids, depth, var,
+                                                        blockIdx.x, smem, nullptr, nullptr, fz);
 }
 
 // Copy rows [off, off + n) of the outputs to their host destinations on
@@ -106,7 +107,18 @@ bg_status launch_k(const HashView& h, const GridView& g, int k, const OkParams& 
     if (rc != BG_OK) return rc;
     int* flag = (int*)scratch;
     const int gx = (g.nx + 15) / 16;
-    const int64_t sys_per_block = (int64_t)kSolveWarps * Gm::SYS * kRounds;
+    const int64_t sys_per_block = (int64_t)kGridSolveWarps * Gm::SYS * kRounds;
+    const int smem_bytes = kGridSolveWarps * Gm::WARP_FLOATS * (int)sizeof(float);
+    cudaError_t ea = cudaFuncSetAttribute(k_okrige_solve<K, false>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+    if constexpr (K == 32)
+        if (ea == cudaSuccess)
+            ea = cudaFuncSetAttribute(k_okrige_solve<K, true>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+    if (ea != cudaSuccess) {
+        dfree(ctx, scratch, flag_bytes + id_bytes, st);
+        return cuda_fail(ea, "solve shared-memory size");
+    }
     for (int64_t j0 = 0; j0 < g.ny; j0 += rows) {
         const int64_t j1 = std::min<int64_t>(g.ny, j0 + rows);
         const int64_t nb = (int64_t)gx * ((j1 - j0 + 7) / 8);
@@ -130,13 +142,13 @@ bg_status launch_k(const HashView& h, const GridView& g, int k, const OkParams& 
             bool fused = false;
             if constexpr (K == 32) {  // the fused IDW runs with 8 threads per system
                 if (fz) {
-                    k_okrige_solve<K, true><<<(unsigned)sb, kSolveWarps * 32, 0, st>>>(
+                    k_okrige_solve<K, true><<<(unsigned)sb, kGridSolveWarps * 32, smem_bytes, st>>>(
                         h, g, k, p, j0 * g.nx, nodes, chunk_ids, depth, var, *fz);
                     fused = true;
                 }
             }
             if (!fused)
-                k_okrige_solve<K, false><<<(unsigned)sb, kSolveWarps * 32, 0, st>>>(
+                k_okrige_solve<K, false><<<(unsigned)sb, kGridSolveWarps * 32, smem_bytes, st>>>(
                     h, g, k, p, j0 * g.nx, nodes, chunk_ids, depth, var, IdwFuse{});
         }
         note_launches(3);
@@ -192,13 +204,14 @@ __global__ void __launch_bounds__(128) k_knn_ids_pts_wide(HashView h, PointsView
         knn_ids_point_wide<K>(h, __ldg(q.x + p), __ldg(q.y + p), k, ids + (p - p0) * k);
 }
 
+// dynamic shared memory: kGridSolveWarps * Geo<K>::WARP_FLOATS floats
 template <int K>
-__global__ void __launch_bounds__(kSolveWarps * 32, kSolveBlocksPerSM) k_okrige_solve_pts(
+__global__ void __launch_bounds__(kGridSolveWarps * 32, kGridSolveBlocksPerSM) k_okrige_solve_pts(
     HashView h, PointsView q, int k, OkParams p, int64_t p0, int64_t nodes,
     const int32_t* __restrict__ ids, float* __restrict__ depth, float* __restrict__ var) {
-    __shared__ __align__(16) float smem[kSolveWarps * Geo<K>::WARP_FLOATS];
-    okrige_solve_block<K, true>(h, GridView{}, k, p, p0, nodes, ids, depth, var, blockIdx.x, smem,
-                                q.x, q.y);
+    extern __shared__ __align__(16) float smem[];
+    okrige_solve_block<K, true, false, kGridSolveWarps>(h, GridView{}, k, p, p0, nodes, ids, depth,
+                                                        var, blockIdx.x, smem, q.x, q.y);
 }
 
 template <int K>
@@ -215,7 +228,14 @@ bg_status launch_pts_k(const HashView& h, const PointsView& q, int k, const OkPa
     bg_status rc = dalloc(ctx, &scratch, flag_bytes + id_bytes, st);
     if (rc != BG_OK) return rc;
     int* flag = (int*)scratch;
-    const int64_t sys_per_block = (int64_t)kSolveWarps * Gm::SYS * kRounds;
+    const int64_t sys_per_block = (int64_t)kGridSolveWarps * Gm::SYS * kRounds;
+    const int smem_bytes = kGridSolveWarps * Gm::WARP_FLOATS * (int)sizeof(float);
+    const cudaError_t ea = cudaFuncSetAttribute(
+        k_okrige_solve_pts<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+    if (ea != cudaSuccess) {
+        dfree(ctx, scratch, flag_bytes + id_bytes, st);
+        return cuda_fail(ea, "solve shared-memory size");
+    }
     for (int64_t p0 = 0; p0 < q.m; p0 += per) {
         const int64_t p1 = std::min<int64_t>(q.m, p0 + per);
         const int64_t n = p1 - p0;
@@ -235,8 +255,8 @@ bg_status launch_pts_k(const HashView& h, const PointsView& q, int k, const OkPa
         const int64_t sb = (n + sys_per_block - 1) / sys_per_block;
         {
             ProfScope ps(ctx, kProfSolve, n, st);
-            k_okrige_solve_pts<K><<<(unsigned)sb, kSolveWarps * 32, 0, st>>>(h, q, k, p, p0, n,
-                                                                             chunk_ids, depth, var);
+            k_okrige_solve_pts<K><<<(unsigned)sb, kGridSolveWarps * 32, smem_bytes, st>>>(
+                h, q, k, p, p0, n, chunk_ids, depth, var);
         }
         note_launches(3);
         e = cudaGetLastError();

@@ -44,10 +44,14 @@ namespace bg {
 
 
 constexpr int kR = 4;            // rows per thread
-constexpr int kSolveWarps = 4;   // warps per solve block
+constexpr int kSolveWarps = 4;   // warps per solve block (batched kernels)
 constexpr int kRounds = 1;       // system batches per warp (one: more, shorter blocks balance best)
-constexpr int kSolveBlocksPerSM = 4;  // launch bound: 16 warps resident (128 registers)
 constexpr int kBwdLook = 2;      // back-sweep pipeline depth (see bwd_step)
+// The grid and point-list solve kernels run 8-warp blocks, 2 per SM (the same
+// 16 warps): with the unrolled solve's long instruction stream, two blocks in
+// different phases fetch far fewer distinct instructions than four.
+constexpr int kGridSolveWarps = 8;
+constexpr int kGridSolveBlocksPerSM = 2;
 
 template <int K>
 struct Geo {
@@ -341,15 +345,15 @@ __device__ __forceinline__ float pow2f(int e) { return __int_as_float((127 + e) 
 // exponent e with 2^(e-1) <= v < 2^e for finite v > 0
 __device__ __forceinline__ int exp_above(float v) { return ((__float_as_int(v) >> 23) & 0xff) - 126; }
 
-// The kriging systems of solve block `blk` (kSolveWarps warps x SYS systems x
+// The kriging systems of solve block `blk` (kWarps warps x SYS systems x
 // kRounds rounds) of a range of `nodes` grid nodes starting at node0, with the
-// neighbour ids of node node0 + i at ids[i * k]. smem: kSolveWarps * WARP_FLOATS.
+// neighbour ids of node node0 + i at ids[i * k]. smem: kWarps * WARP_FLOATS.
 // With kPts the "nodes" are query points whose coordinates are px[], py[]
 // (g unused).
 // With kIdw the block also writes the IDW depth over the first fz.k of the
 // node's sorted neighbours (fz.k <= k): the same value bg_interp_idw gives, as
 // its operations are those of idw_from in the same order.
-template <int K, bool kPts = false, bool kIdw = false>
+template <int K, bool kPts = false, bool kIdw = false, int kWarps = kSolveWarps>
 __device__ __forceinline__ void okrige_solve_block(const HashView& h, const GridView& g, int k,
                                                    const OkParams& p, int64_t node0, int64_t nodes,
                                                    const int32_t* __restrict__ ids,
@@ -378,7 +382,7 @@ __device__ __forceinline__ void okrige_solve_block(const HashView& h, const Grid
     const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << gbase);
 
     for (int round = 0; round < kRounds; ++round) {
-        const int64_t sys = (blk * kSolveWarps + warp) * (Gm::SYS * kRounds) +
+        const int64_t sys = (blk * kWarps + warp) * (Gm::SYS * kRounds) +
                             (int64_t)round * Gm::SYS + grp;
         const bool live = sys < nodes;  // uniform within a group
         const int64_t node = node0 + (live ? sys : 0);
