@@ -65,7 +65,7 @@ def okrige_fp64_flops_per_node(k=OK_K):
 # from one ncu capture of the current kernel on the 2-line swath (3.384M
 # nodes: 450.4 MB read + 38.3 MB written per launch, mostly the 128 B of
 # neighbour ids per node); traffic grows with the nodes of a launch.
-SOLVE_DRAM_BYTES_PER_NODE = (449.85216e6 + 37.9968e6) / 3.384e6
+SOLVE_DRAM_BYTES_PER_NODE = (452.216064e6 + 38.499584e6) / 3.384e6
 
 # FP32 peak for "alu"-bound roofline: 152 SMs x 128 FP32 lanes x 2 flops/FMA x
 # the maximum SM clock (2,070 MHz) = 80.5 TFLOP/s.
