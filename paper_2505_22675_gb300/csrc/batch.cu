@@ -57,10 +57,12 @@ constexpr int kBT = 256;          // threads of those kernels
 constexpr int kItemThreads = 128;
 constexpr int kKnnThreads = 64;  // k-NN blocks: a 16 KB heap, 13 blocks (26 warps) per SM
 constexpr int kBatchSolveBlocks = 8;  // solve blocks per claimed item: one atomic per 64 systems
-// The persistent solve reads its tile descriptor from shared memory, which
-// raises its register needs: it runs faster with 12 resident warps (no
-// spills) than held to the per-grid kernel's 128 registers.
-constexpr int kBatchSolveBlocksPerSM = 12 / kSolveWarps;
+// The persistent solve runs 8-warp blocks, 2 per SM (128 registers, dynamic
+// shared memory), like the per-grid kernels: two blocks in different phases
+// of the long unrolled solve wait far less for instruction fetch than 3 or 4
+// smaller ones (measured 291 ms per batch against 325 ms for 3 x 4 warps).
+constexpr int kBatchSolveWarps = 8;
+constexpr int kBatchSolveBlocksPerSM = 2;
 
 __device__ __forceinline__ int upper_tile(const int64_t* off, int T, int64_t v) {
     // largest t with off[t] <= v  (off ascending, off[0] = 0)
@@ -320,12 +322,12 @@ __global__ void __launch_bounds__(kKnnThreads) k_batch_knn(
 // descriptor is staged in shared memory so its fields are read where needed
 // instead of being held in registers across the solve
 template <int K>
-__global__ void __launch_bounds__(kSolveWarps * 32, kBatchSolveBlocksPerSM) k_batch_solve(
+__global__ void __launch_bounds__(kBatchSolveWarps * 32, kBatchSolveBlocksPerSM) k_batch_solve(
     const TileDesc* __restrict__ td, const int* __restrict__ tiles, int nt,
     const int64_t* __restrict__ off, int64_t items, unsigned long long* __restrict__ ctr,
     const int4* __restrict__ orig, const int4* __restrict__ rec, const int* __restrict__ cell_start,
     const int* __restrict__ sat) {
-    __shared__ __align__(16) float smem[kSolveWarps * Geo<K>::WARP_FLOATS];
+    extern __shared__ __align__(16) float smem[];
     __shared__ long long s_item;
     __shared__ int s_j;
     __shared__ HashView s_h;
@@ -355,8 +357,8 @@ __global__ void __launch_bounds__(kSolveWarps * 32, kBatchSolveBlocksPerSM) k_ba
         if (item >= items) break;
         const int64_t b0 = (item - __ldg(off + s_j)) * kBatchSolveBlocks;
         for (int b = 0; b < kBatchSolveBlocks; ++b)
-            okrige_solve_block<K>(s_h, s_g, s_k, s_p, 0, (int64_t)s_g.nx * s_g.ny, s_ids, s_depth,
-                                  s_var, b0 + b, smem);
+            okrige_solve_block<K, false, false, kBatchSolveWarps>(
+                s_h, s_g, s_k, s_p, 0, (int64_t)s_g.nx * s_g.ny, s_ids, s_depth, s_var, b0 + b, smem);
         __syncthreads();  // the next item overwrites the staged descriptor
     }
 }
@@ -492,7 +494,7 @@ void enqueue_batch(bg_batch_s* b, cudaStream_t st) {
         const unsigned grid = (unsigned)std::min<int64_t>(G.items, 152 * kBatchSolveBlocksPerSM);
         unsigned long long* ctr = b->d_ctr + 1 + gi;
 #define BG_SOLVE(KK)                                                                              \
-    k_batch_solve<KK><<<grid, kSolveWarps * 32, 0, st>>>(b->d_desc, G.tiles, G.nt, G.off, G.items, \
+    k_batch_solve<KK><<<grid, kBatchSolveWarps * 32, kBatchSolveWarps * Geo<KK>::WARP_FLOATS * 4, st>>>(b->d_desc, G.tiles, G.nt, G.off, G.items, \
                                                         ctr, b->d_orig, b->d_rec,                 \
                                                         b->d_cell_start, b->d_sat)
         switch (G.K) {
@@ -504,6 +506,17 @@ void enqueue_batch(bg_batch_s* b, cudaStream_t st) {
 #undef BG_SOLVE
         note_launches(1);
     }
+}
+
+cudaError_t set_batch_solve_smem() {
+    cudaError_t e = cudaSuccess;
+#define BG_SMEM(KK)                                                                          \
+    if (e == cudaSuccess)                                                                    \
+        e = cudaFuncSetAttribute(k_batch_solve<KK>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                 kBatchSolveWarps * Geo<KK>::WARP_FLOATS * 4);
+    BG_SMEM(4) BG_SMEM(8) BG_SMEM(16) BG_SMEM(32)
+#undef BG_SMEM
+    return e;
 }
 
 bg_status drop_graph(bg_batch_s* b) {
@@ -632,7 +645,8 @@ bg_status bg_batch_create(bg_ctx_t ctx, const bg_tile* tiles, int n_tiles, bg_ba
     int prev = 0;
     cudaGetDevice(&prev);
     cudaSetDevice(ctx->device);
-    cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+    cudaError_t e = set_batch_solve_smem();
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming);
     st = b->stream;
@@ -669,7 +683,7 @@ bg_status bg_batch_create(bg_ctx_t ctx, const bg_tile* tiles, int n_tiles, bg_ba
         if (gt[q].empty()) continue;
         bg_batch_s::Group G{Ks[q], (int)gt[q].size(), 0, (int*)(base + o_gt[q]),
                             (int64_t*)(base + o_go[q])};
-        const int sys_per_item = kSolveWarps * (32 / (Ks[q] / kR)) * kRounds * kBatchSolveBlocks;
+        const int sys_per_item = kBatchSolveWarps * (32 / (Ks[q] / kR)) * kRounds * kBatchSolveBlocks;
         std::vector<int64_t> go(gt[q].size() + 1, 0);
         for (size_t j = 0; j < gt[q].size(); ++j) {
             const TileDesc& d = b->host_desc[gt[q][j]];
