@@ -56,7 +56,7 @@ constexpr int kChunk = 4096;      // soundings per block in the per-sounding ker
 constexpr int kBT = 256;          // threads of those kernels
 constexpr int kItemThreads = 128;
 constexpr int kKnnThreads = 64;  // k-NN blocks: a 16 KB heap, 13 blocks (26 warps) per SM
-constexpr int kBatchSolveBlocks = 8;  // solve blocks per claimed item: one atomic per 64 systems
+constexpr int kBatchSolveBlocks = 8;  // block batches per claimed item (256 systems at K = 32), one atomic
 // The persistent solve runs 8-warp blocks, 2 per SM (128 registers, dynamic
 // shared memory), like the per-grid kernels: two blocks in different phases
 // of the long unrolled solve wait far less for instruction fetch than 3 or 4
