@@ -349,21 +349,23 @@ bg_status bg_batch_destroy(bg_batch_t b);
 /* ------------------------------------------------- allocation-free IDW */
 
 /* IDW gridding that allocates no device memory, for callers that cannot call
- * cudaMalloc (code run inside host callbacks or driver-owned threads, runtimes
- * whose allocator policy forbids it, or processes that reserve all device
- * memory up front). The paper has no counterpart: this is a deployment
- * variant of bg_soundings_upload + bg_interp_idw with the same results.
+ * cudaMalloc: processes that reserve all device memory up front, runtimes
+ * whose allocator policy forbids device allocation on their worker threads,
+ * and driver-owned threads that must not allocate. The paper has no
+ * counterpart: this is a deployment variant of bg_soundings_upload +
+ * bg_interp_idw with bitwise the same results.
  *   x_cm, y_cm, z_m: DEVICE pointers, n values each, n <= 262144 (larger n
  *     returns BG_ERR_INVALID_ARG before any device work).
  *   Grid (x0_cm, y0_cm, cell_cm, nx, ny), k, power, depth_out, nbr_out: as
  *     for bg_grid_create and bg_interp_idw; outputs are device pointers.
- *   cuda_stream: cudaStream_t; the call synchronizes it once (bounding box).
+ *   cuda_stream: cudaStream_t; the call synchronizes it once (bounding box),
+ *     so it must not be made inside stream capture, nor from a CUDA stream
+ *     callback (where CUDA calls are not allowed).
  * Work space: one 16 MiB file-scope __device__ array that every device loading
- * the library holds until the process exits. The first call on a device looks
- * up that array's address (cudaGetSymbolAddress) with the device current;
- * make that first call before any stream capture. Every call shares the array
- * and clears what must start at zero; calls whose GPU work overlaps race on
- * it, so do not run two at once. No context is needed. */
+ * the library holds until the process exits; each call looks up its device
+ * address (cudaGetSymbolAddress) with the caller's device current. Every call
+ * shares the array and clears what must start at zero; calls whose GPU work
+ * overlaps race on it, so do not run two at once. No context is needed. */
 bg_status bg_interp_idw_noalloc(const int32_t* x_cm, const int32_t* y_cm, const float* z_m,
                                 int64_t n, int32_t x0_cm, int32_t y0_cm, int32_t cell_cm,
                                 int32_t nx, int32_t ny, int k, float power, float* depth_out,

@@ -1,6 +1,10 @@
 """FP64 CPU oracle for exact k-NN, IDW, ordinary kriging and gridded
 bilinear / Catmull-Rom resampling (ctypes over oracle.c).
 
+The k-NN is brute force by default; `Tree` builds a 2-d tree over the same
+soundings that gives the same (d2, index)-ordered neighbours far faster on
+large inputs (pass it as `tree=` to knn, idw and okrige).
+
 TEST INFRASTRUCTURE ONLY: the test suite, the smoke check and the CPU-baseline
 leg of the benchmark may import this package; the library under
 paper_2505_22675_gb300/ never does, and shares no code with it.
@@ -47,12 +51,12 @@ def _load():
     i32, i64, dbl = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
     lib.oracle_grid_nodes.argtypes = [i32, i32, i32, i32, i32, P, P]
     lib.oracle_grid_nodes.restype = None
-    lib.oracle_knn.argtypes = [P, P, P, i64, P, P, i64, ctypes.c_int, P, P, P, ctypes.c_int]
+    lib.oracle_knn.argtypes = [P, P, P, i64, P, P, i64, ctypes.c_int, P, P, P, ctypes.c_int, P]
     lib.oracle_knn.restype = ctypes.c_int
-    lib.oracle_idw.argtypes = [P, P, P, i64, P, P, i64, ctypes.c_int, dbl, P, P, ctypes.c_int]
+    lib.oracle_idw.argtypes = [P, P, P, i64, P, P, i64, ctypes.c_int, dbl, P, P, ctypes.c_int, P]
     lib.oracle_idw.restype = ctypes.c_int
     lib.oracle_okrige.argtypes = [P, P, P, i64, P, P, i64, ctypes.c_int, ctypes.c_int,
-                                  dbl, dbl, dbl, P, P, P, P, P, ctypes.c_int]
+                                  dbl, dbl, dbl, P, P, P, P, P, ctypes.c_int, P]
     lib.oracle_okrige.restype = ctypes.c_int
     lib.oracle_variogram.argtypes = [ctypes.c_int, dbl, dbl, dbl, dbl]
     lib.oracle_variogram.restype = dbl
@@ -60,6 +64,10 @@ def _load():
     lib.oracle_solve.restype = ctypes.c_int
     lib.oracle_resample.argtypes = [P, i32, i32, i32, i32, i32, ctypes.c_int, P, P, i64, P, P]
     lib.oracle_resample.restype = ctypes.c_int
+    lib.oracle_tree_build.argtypes = [P, P, P, i64]
+    lib.oracle_tree_build.restype = P
+    lib.oracle_tree_free.argtypes = [P]
+    lib.oracle_tree_free.restype = None
     lib.oracle_threads.argtypes = [ctypes.c_int]
     lib.oracle_threads.restype = ctypes.c_int
     _lib = lib
@@ -81,6 +89,45 @@ def _inputs(x, y, z, qx, qy):
     return x, y, z, qx, qy
 
 
+class Tree:
+    """2-d tree over the valid soundings of (x, y, z), for knn / idw / okrige
+    on large inputs. It keeps references to the arrays it was built from;
+    pass the same x, y, z to the queries."""
+
+    def __init__(self, x, y, z):
+        self.x = np.ascontiguousarray(x, dtype=np.int32)
+        self.y = np.ascontiguousarray(y, dtype=np.int32)
+        self.z = np.ascontiguousarray(z, dtype=np.float32)
+        if not (self.x.shape == self.y.shape == self.z.shape):
+            raise ValueError("shape mismatch")
+        self._h = _load().oracle_tree_build(_p(self.x), _p(self.y), _p(self.z), self.x.size)
+        if not self._h:
+            raise MemoryError("oracle_tree_build")
+
+    def handle(self, x, y, z):
+        """The tree's handle, after checking it was built from these arrays."""
+        for a, b in ((x, self.x), (y, self.y), (z, self.z)):
+            a = np.asarray(a)
+            if a.shape != b.shape or not (a is b or np.array_equal(a, b, equal_nan=True)):
+                raise ValueError("the tree was built from other soundings")
+        return ctypes.c_void_p(self._h)
+
+    def close(self):
+        if self._h:
+            _load().oracle_tree_free(ctypes.c_void_p(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _tree(tree, x, y, z):
+    return None if tree is None else tree.handle(x, y, z)
+
+
 def threads(requested: int = 0) -> int:
     """Threads the oracle uses for `requested` (0 = every online core)."""
     return int(_load().oracle_threads(requested))
@@ -94,28 +141,29 @@ def grid_nodes(x0_cm: int, y0_cm: int, cell_cm: int, nx: int, ny: int):
     return qx, qy
 
 
-def knn(x, y, z, qx, qy, k: int, nthreads: int = 0):
-    """Exact k-NN by brute force: (idx int32[m,k], d2 int64[m,k], keff int32[m]); -1 pads."""
+def knn(x, y, z, qx, qy, k: int, nthreads: int = 0, tree: Tree | None = None):
+    """Exact k-NN (brute force, or `tree`): (idx int32[m,k], d2 int64[m,k], keff int32[m]); -1 pads."""
     x, y, z, qx, qy = _inputs(x, y, z, qx, qy)
     m = qx.size
     idx = np.empty((m, k), dtype=np.int32)
     d2 = np.empty((m, k), dtype=np.int64)
     keff = np.empty(m, dtype=np.int32)
     rc = _load().oracle_knn(_p(x), _p(y), _p(z), x.size, _p(qx), _p(qy), m, k,
-                            _p(idx), _p(d2), _p(keff), nthreads)
+                            _p(idx), _p(d2), _p(keff), nthreads, _tree(tree, x, y, z))
     if rc != 0:
         raise ValueError("oracle_knn: bad arguments")
     return idx, d2, keff
 
 
-def idw(x, y, z, qx, qy, k: int, power: float = 2.0, nthreads: int = 0, want_idx: bool = False):
+def idw(x, y, z, qx, qy, k: int, power: float = 2.0, nthreads: int = 0, want_idx: bool = False,
+        tree: Tree | None = None):
     """FP64 IDW depth per node (NaN where no valid sounding exists)."""
     x, y, z, qx, qy = _inputs(x, y, z, qx, qy)
     m = qx.size
     depth = np.empty(m, dtype=np.float64)
     idx = np.empty((m, k), dtype=np.int32) if want_idx else None
     rc = _load().oracle_idw(_p(x), _p(y), _p(z), x.size, _p(qx), _p(qy), m, k, float(power),
-                            _p(depth), _p(idx), nthreads)
+                            _p(depth), _p(idx), nthreads, _tree(tree, x, y, z))
     if rc != 0:
         raise ValueError("oracle_idw: bad arguments")
     return (depth, idx) if want_idx else depth
@@ -123,7 +171,7 @@ def idw(x, y, z, qx, qy, k: int, power: float = 2.0, nthreads: int = 0, want_idx
 
 def okrige(x, y, z, qx, qy, k: int, model: int = SPHERICAL, nugget: float = 0.25,
            sill: float = 100.0, range_m: float = 50.0, nthreads: int = 0,
-           want_weights: bool = False, want_idx: bool = False):
+           want_weights: bool = False, want_idx: bool = False, tree: Tree | None = None):
     """FP64 ordinary kriging: (depth, variance[, lambda[m,k], mu[m]][, idx])."""
     x, y, z, qx, qy = _inputs(x, y, z, qx, qy)
     m = qx.size
@@ -134,7 +182,7 @@ def okrige(x, y, z, qx, qy, k: int, model: int = SPHERICAL, nugget: float = 0.25
     idx = np.empty((m, k), dtype=np.int32) if want_idx else None
     rc = _load().oracle_okrige(_p(x), _p(y), _p(z), x.size, _p(qx), _p(qy), m, k, int(model),
                                float(nugget), float(sill), float(range_m), _p(depth), _p(var),
-                               _p(lam), _p(mu), _p(idx), nthreads)
+                               _p(lam), _p(mu), _p(idx), nthreads, _tree(tree, x, y, z))
     if rc != 0:
         raise ValueError("oracle_okrige: bad arguments")
     out = [depth, var]

@@ -10,6 +10,9 @@
  *   - exact k nearest neighbours of a grid node by brute force: every valid
  *     sounding (depth not NaN, the "valid candidate neighbours" of Sec. III-B
  *     and III-D) ranked by (squared distance in int64 cm^2, upload index);
+ *     for large inputs the same k smallest (d2, index) pairs come from a 2-d
+ *     tree (median splits, bounding boxes, lexicographic insertion), which
+ *     the tests hold equal to the brute force;
  *   - inverse-distance weighting over those neighbours in FP64;
  *   - local ordinary kriging (Sec. III-C): the variogram gamma(h) of the
  *     neighbours, the bordered system [Gamma 1; 1^T 0][lambda; mu] =
@@ -152,6 +155,213 @@ static int knn_one(const int32_t* x, const int32_t* y, const float* z, int64_t n
     return cnt;
 }
 
+/* ---------------------------------------------------------- 2-d tree */
+
+/* A 2-d tree over the valid soundings: the same k smallest (d2, index) pairs
+ * as knn_one, found without visiting every sounding. Build: the points of a
+ * node (a contiguous range of the tree-ordered array) are split at their
+ * median along the longer side of the node's bounding box; node i's children
+ * are 2i + 1 (lower half) and 2i + 2. Ranges of at most TREE_LEAF points are
+ * leaves. Query: visit the nearer child first and skip a node whose box lies
+ * farther than the current k-th distance (a box exactly at that distance is
+ * still visited: an equally distant point with a lower index would win). */
+#define TREE_LEAF 8
+
+typedef struct {
+    int32_t x, y, id;
+} tree_pt;
+
+typedef struct {
+    int64_t n;        /* valid soundings in the tree */
+    tree_pt* pt;      /* tree order */
+    int32_t* box;     /* 4 per node: x0, y0, x1, y1 (inclusive) */
+    int64_t nodes;    /* node slots (heap numbering) */
+} oracle_tree;
+
+static int32_t pt_key(const tree_pt* p, int axis) { return axis ? p->y : p->x; }
+
+/* Reorder a[lo, hi) so that a[mid] holds the element of rank mid - lo along
+ * the axis, with no larger key before it and no smaller after it. Each round
+ * splits the range three ways around a pivot key taken from it (below, equal,
+ * above); the equal part is never empty, so every round shrinks the range. */
+static void select_median(tree_pt* a, int64_t lo, int64_t hi, int64_t mid, int axis) {
+    while (hi - lo > 1) {
+        const int32_t k0 = pt_key(&a[lo], axis), k1 = pt_key(&a[lo + (hi - lo) / 2], axis);
+        const int32_t k2 = pt_key(&a[hi - 1], axis);
+        const int32_t piv = k0 < k1 ? (k1 < k2 ? k1 : (k0 < k2 ? k2 : k0))
+                                    : (k0 < k2 ? k0 : (k1 < k2 ? k2 : k1));
+        int64_t lt = lo, i = lo, gt = hi;  /* [lo, lt) < piv, [lt, i) = piv, [gt, hi) > piv */
+        while (i < gt) {
+            const int32_t key = pt_key(&a[i], axis);
+            if (key < piv) {
+                tree_pt t = a[lt];
+                a[lt++] = a[i];
+                a[i++] = t;
+            } else if (key > piv) {
+                tree_pt t = a[--gt];
+                a[gt] = a[i];
+                a[i] = t;
+            } else {
+                ++i;
+            }
+        }
+        if (mid < lt) hi = lt;
+        else if (mid >= gt) lo = gt;
+        else return;
+    }
+}
+
+typedef struct {
+    oracle_tree* t;
+    int64_t node, lo, hi;
+    int depth;
+} build_job;
+
+static void* build_node(void* p);
+
+static void build_range(oracle_tree* t, int64_t node, int64_t lo, int64_t hi, int depth) {
+    int32_t x0 = INT32_MAX, y0 = INT32_MAX, x1 = INT32_MIN, y1 = INT32_MIN;
+    for (int64_t j = lo; j < hi; ++j) {
+        const tree_pt* q = &t->pt[j];
+        if (q->x < x0) x0 = q->x;
+        if (q->x > x1) x1 = q->x;
+        if (q->y < y0) y0 = q->y;
+        if (q->y > y1) y1 = q->y;
+    }
+    int32_t* b = t->box + 4 * node;
+    b[0] = x0;
+    b[1] = y0;
+    b[2] = x1;
+    b[3] = y1;
+    if (hi - lo <= TREE_LEAF) return;
+    const int axis = ((int64_t)y1 - y0) > ((int64_t)x1 - x0) ? 1 : 0;
+    const int64_t mid = lo + (hi - lo) / 2;
+    select_median(t->pt, lo, hi, mid, axis);
+    /* the two halves are disjoint: build the lower one on a new thread near the root */
+    if (depth < 4) {
+        build_job job = {t, 2 * node + 1, lo, mid, depth + 1};
+        pthread_t th;
+        if (pthread_create(&th, NULL, build_node, &job) == 0) {
+            build_range(t, 2 * node + 2, mid, hi, depth + 1);
+            pthread_join(th, NULL);
+            return;
+        }
+    }
+    build_range(t, 2 * node + 1, lo, mid, depth + 1);
+    build_range(t, 2 * node + 2, mid, hi, depth + 1);
+}
+
+static void* build_node(void* p) {
+    build_job* j = (build_job*)p;
+    build_range(j->t, j->node, j->lo, j->hi, j->depth);
+    return NULL;
+}
+
+void oracle_tree_free(void* p) {
+    oracle_tree* t = (oracle_tree*)p;
+    if (!t) return;
+    free(t->pt);
+    free(t->box);
+    free(t);
+}
+
+/* Build the tree over the valid soundings of (x, y, z). Returns NULL when
+ * memory runs out. The tree keeps copies of the coordinates and upload
+ * indices; queries still read depths from the caller's arrays. */
+void* oracle_tree_build(const int32_t* x, const int32_t* y, const float* z, int64_t n) {
+    oracle_tree* t = (oracle_tree*)calloc(1, sizeof(oracle_tree));
+    if (!t || n < 0) {
+        free(t);
+        return NULL;
+    }
+    int64_t nv = 0;
+    for (int64_t p = 0; p < n; ++p)
+        if (!isnan(z[p])) ++nv;
+    t->n = nv;
+    t->pt = (tree_pt*)malloc(sizeof(tree_pt) * (size_t)(nv > 0 ? nv : 1));
+    /* the largest range at depth d holds ceil(nv / 2^d) points */
+    int depth = 0;
+    for (int64_t s = nv; s > TREE_LEAF; s = (s + 1) / 2) ++depth;
+    t->nodes = nv > 0 ? ((int64_t)1 << (depth + 1)) - 1 : 0;
+    t->box = (int32_t*)malloc(sizeof(int32_t) * 4 * (size_t)(t->nodes > 0 ? t->nodes : 1));
+    if (!t->pt || !t->box) {
+        oracle_tree_free(t);
+        return NULL;
+    }
+    int64_t j = 0;
+    for (int64_t p = 0; p < n; ++p)
+        if (!isnan(z[p])) {
+            t->pt[j].x = x[p];
+            t->pt[j].y = y[p];
+            t->pt[j].id = (int32_t)p;
+            ++j;
+        }
+    if (nv > 0) build_range(t, 0, 0, nv, 0);
+    return t;
+}
+
+/* Keep the k smallest (d2, index) pairs in ascending order in bd/bi. */
+static void insert_lex(int k, int* cnt, int32_t* bi, int64_t* bd, int64_t d2, int32_t id) {
+    if (*cnt == k && (d2 > bd[k - 1] || (d2 == bd[k - 1] && id > bi[k - 1]))) return;
+    int i = *cnt < k ? *cnt : k - 1;
+    while (i > 0 && (bd[i - 1] > d2 || (bd[i - 1] == d2 && bi[i - 1] > id))) {
+        bd[i] = bd[i - 1];
+        bi[i] = bi[i - 1];
+        --i;
+    }
+    bd[i] = d2;
+    bi[i] = id;
+    if (*cnt < k) ++*cnt;
+}
+
+/* Squared distance from (qx, qy) to the nearest point of a node's box. */
+static int64_t box_d2(const int32_t* b, int32_t qx, int32_t qy) {
+    int64_t dx = 0, dy = 0;
+    if (qx < b[0]) dx = (int64_t)b[0] - qx;
+    else if (qx > b[2]) dx = (int64_t)qx - b[2];
+    if (qy < b[1]) dy = (int64_t)b[1] - qy;
+    else if (qy > b[3]) dy = (int64_t)qy - b[3];
+    return dx * dx + dy * dy;
+}
+
+static void tree_visit(const oracle_tree* t, int64_t node, int64_t lo, int64_t hi, int32_t qx,
+                       int32_t qy, int k, int* cnt, int32_t* bi, int64_t* bd) {
+    if (*cnt == k && box_d2(t->box + 4 * node, qx, qy) > bd[k - 1]) return;
+    if (hi - lo <= TREE_LEAF) {
+        for (int64_t j = lo; j < hi; ++j) {
+            const tree_pt* q = &t->pt[j];
+            const int64_t dx = (int64_t)q->x - qx, dy = (int64_t)q->y - qy;
+            insert_lex(k, cnt, bi, bd, dx * dx + dy * dy, q->id);
+        }
+        return;
+    }
+    const int64_t mid = lo + (hi - lo) / 2, l = 2 * node + 1, r = 2 * node + 2;
+    if (box_d2(t->box + 4 * l, qx, qy) <= box_d2(t->box + 4 * r, qx, qy)) {
+        tree_visit(t, l, lo, mid, qx, qy, k, cnt, bi, bd);
+        tree_visit(t, r, mid, hi, qx, qy, k, cnt, bi, bd);
+    } else {
+        tree_visit(t, r, mid, hi, qx, qy, k, cnt, bi, bd);
+        tree_visit(t, l, lo, mid, qx, qy, k, cnt, bi, bd);
+    }
+}
+
+static int tree_knn_one(const oracle_tree* t, int32_t qx, int32_t qy, int k, int32_t* bi,
+                        int64_t* bd) {
+    int cnt = 0;
+    if (t->n > 0) tree_visit(t, 0, 0, t->n, qx, qy, k, &cnt, bi, bd);
+    for (int i = cnt; i < k; ++i) {
+        bd[i] = -1;
+        bi[i] = -1;
+    }
+    return cnt;
+}
+
+/* k nearest of (qx, qy): from the tree when one is given, else brute force. */
+static int nearest(const oracle_tree* t, const int32_t* x, const int32_t* y, const float* z,
+                   int64_t n, int32_t qx, int32_t qy, int k, int32_t* bi, int64_t* bd) {
+    return t ? tree_knn_one(t, qx, qy, k, bi, bd) : knn_one(x, y, z, n, qx, qy, k, bi, bd);
+}
+
 typedef struct {
     const int32_t *x, *y;
     const float* z;
@@ -161,22 +371,25 @@ typedef struct {
     int32_t* idx;
     int64_t* d2;
     int32_t* keff;
+    const oracle_tree* tree;
 } knn_args;
 
 static void knn_range(void* p, int64_t lo, int64_t hi) {
     knn_args* a = (knn_args*)p;
     for (int64_t q = lo; q < hi; ++q) {
-        int c = knn_one(a->x, a->y, a->z, a->n, a->qx[q], a->qy[q], a->k,
+        int c = nearest(a->tree, a->x, a->y, a->z, a->n, a->qx[q], a->qy[q], a->k,
                         a->idx + q * a->k, a->d2 + q * a->k);
         if (a->keff) a->keff[q] = c;
     }
 }
 
+/* tree: NULL for brute force, else a tree built from the same x, y, z. */
 int oracle_knn(const int32_t* x, const int32_t* y, const float* z, int64_t n,
                const int32_t* qx, const int32_t* qy, int64_t m, int k,
-               int32_t* idx_out, int64_t* d2_out, int32_t* keff_out, int nthreads) {
+               int32_t* idx_out, int64_t* d2_out, int32_t* keff_out, int nthreads,
+               const void* tree) {
     if (k <= 0 || n < 0 || m < 0) return -1;
-    knn_args a = {x, y, z, n, qx, qy, k, idx_out, d2_out, keff_out};
+    knn_args a = {x, y, z, n, qx, qy, k, idx_out, d2_out, keff_out, (const oracle_tree*)tree};
     parallel_for(m, nthreads, knn_range, &a);
     return 0;
 }
@@ -209,6 +422,7 @@ typedef struct {
     double power;
     double* depth;
     int32_t* idx;
+    const oracle_tree* tree;
 } idw_args;
 
 static void idw_range(void* p, int64_t lo, int64_t hi) {
@@ -216,7 +430,7 @@ static void idw_range(void* p, int64_t lo, int64_t hi) {
     int32_t* bi = (int32_t*)malloc(sizeof(int32_t) * a->k);
     int64_t* bd = (int64_t*)malloc(sizeof(int64_t) * a->k);
     for (int64_t q = lo; q < hi; ++q) {
-        int c = knn_one(a->x, a->y, a->z, a->n, a->qx[q], a->qy[q], a->k, bi, bd);
+        int c = nearest(a->tree, a->x, a->y, a->z, a->n, a->qx[q], a->qy[q], a->k, bi, bd);
         a->depth[q] = idw_one(a->z, bi, bd, c, a->power);
         if (a->idx) memcpy(a->idx + q * a->k, bi, sizeof(int32_t) * a->k);
     }
@@ -226,9 +440,9 @@ static void idw_range(void* p, int64_t lo, int64_t hi) {
 
 int oracle_idw(const int32_t* x, const int32_t* y, const float* z, int64_t n,
                const int32_t* qx, const int32_t* qy, int64_t m, int k, double power,
-               double* depth_out, int32_t* idx_out, int nthreads) {
+               double* depth_out, int32_t* idx_out, int nthreads, const void* tree) {
     if (k <= 0 || n < 0 || m < 0 || !(power > 0.0)) return -1;
-    idw_args a = {x, y, z, n, qx, qy, k, power, depth_out, idx_out};
+    idw_args a = {x, y, z, n, qx, qy, k, power, depth_out, idx_out, (const oracle_tree*)tree};
     parallel_for(m, nthreads, idw_range, &a);
     return 0;
 }
@@ -355,6 +569,7 @@ typedef struct {
     double nugget, sill, range_m;
     double *depth, *var, *lam, *mu;
     int32_t* idx;
+    const oracle_tree* tree;
 } ok_args;
 
 static void ok_range(void* p, int64_t lo, int64_t hi) {
@@ -366,7 +581,7 @@ static void ok_range(void* p, int64_t lo, int64_t hi) {
     double* b = (double*)malloc(sizeof(double) * (k + 1));
     double* s = (double*)malloc(sizeof(double) * (k + 1));
     for (int64_t q = lo; q < hi; ++q) {
-        int c = knn_one(a->x, a->y, a->z, a->n, a->qx[q], a->qy[q], k, bi, bd);
+        int c = nearest(a->tree, a->x, a->y, a->z, a->n, a->qx[q], a->qy[q], k, bi, bd);
         double* lam = a->lam ? a->lam + q * k : NULL;
         if (lam)
             for (int i = 0; i < k; ++i) lam[i] = 0.0;
@@ -386,12 +601,12 @@ int oracle_okrige(const int32_t* x, const int32_t* y, const float* z, int64_t n,
                   const int32_t* qx, const int32_t* qy, int64_t m, int k, int model,
                   double nugget, double sill, double range_m, double* depth_out,
                   double* var_out, double* lambda_out, double* mu_out, int32_t* idx_out,
-                  int nthreads) {
+                  int nthreads, const void* tree) {
     if (k <= 0 || n < 0 || m < 0) return -1;
     if (model != ORACLE_SPHERICAL && model != ORACLE_EXPONENTIAL) return -1;
     if (!(range_m > 0.0) || nugget < 0.0 || !(sill > nugget)) return -1;
     ok_args a = {x, y, z, n, qx, qy, k, model, nugget, sill, range_m,
-                 depth_out, var_out, lambda_out, mu_out, idx_out};
+                 depth_out, var_out, lambda_out, mu_out, idx_out, (const oracle_tree*)tree};
     parallel_for(m, nthreads, ok_range, &a);
     return 0;
 }

@@ -1,8 +1,8 @@
 // bg_interp_idw_noalloc: IDW gridding for callers that cannot allocate device
-// memory — code running where cudaMalloc is not allowed (inside a host
-// callback or a driver-owned thread, under an allocator-free runtime policy,
-// or in a process whose memory is fully reserved up front). The work space
-// that bg_soundings_upload and bg_interp_idw would allocate lives here in one
+// memory: a process that reserves all device memory up front, a runtime whose
+// allocator policy forbids cudaMalloc on its worker threads, or code in a
+// driver-owned thread that must not allocate. The work space that
+// bg_soundings_upload and bg_interp_idw would allocate lives here in one
 // file-scope __device__ array instead.
 //
 // The array is a fixed 16 MiB in every device that loads this library, held
@@ -11,8 +11,10 @@
 // accumulator, the wide-pass flag) are cleared by each call. Two calls whose
 // GPU work overlaps (on two streams, or from two host threads) race on the
 // array: run them one after another.
-#include <mutex>
-
+//
+// The call launches kernels and synchronizes its stream once, so it must not
+// be made from a CUDA stream callback (cudaLaunchHostFunc; CUDA calls are not
+// allowed there) or while the stream is being captured.
 #include "bg_internal.h"
 
 namespace {
@@ -23,26 +25,17 @@ constexpr size_t kScratchBytes = size_t(16) << 20;    // 16 MiB
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_setup_mu;
-unsigned char* g_scratch_ptr[kMaxDevices] = {};
-
 size_t up256(size_t v) { return (v + 255) & ~size_t(255); }
 
-// Device address of g_scratch on the current device; looked up once per device.
-bg_status scratch_address(int dev, unsigned char** out) {
-    if (dev < 0 || dev >= kMaxDevices) {
-        bg::set_error("device index beyond the supported range");
-        return BG_ERR_INVALID_ARG;
-    }
-    std::lock_guard<std::mutex> lk(g_setup_mu);
-    if (!g_scratch_ptr[dev]) {
-        void* p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
-        if (e != cudaSuccess) return bg::cuda_fail(e, "cudaGetSymbolAddress(g_scratch)");
-        g_scratch_ptr[dev] = static_cast<unsigned char*>(p);
-    }
-    *out = g_scratch_ptr[dev];
+// Device address of g_scratch on the current device. In host code the name
+// g_scratch is only a host-side stand-in, so the address is looked up on
+// every call: it is cheap, allocates nothing, and stays right after a
+// cudaDeviceReset or a context re-creation.
+bg_status scratch_address(unsigned char** out) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+    if (e != cudaSuccess) return bg::cuda_fail(e, "cudaGetSymbolAddress(g_scratch)");
+    *out = static_cast<unsigned char*>(p);
     return BG_OK;
 }
 
@@ -90,10 +83,8 @@ extern "C" bg_status bg_interp_idw_noalloc(const int32_t* x_cm, const int32_t* y
             return BG_ERR_INVALID_ARG;
         }
     }
-    int dev = 0;
-    BG_CUDA(cudaGetDevice(&dev));
     unsigned char* base = nullptr;
-    const bg_status rc = scratch_address(dev, &base);
+    const bg_status rc = scratch_address(&base);
     if (rc != BG_OK) return rc;
 
     // carve the array: records, cell tables, scan and SAT partial sums, flags

@@ -44,7 +44,6 @@ namespace bg {
 
 
 constexpr int kR = 4;            // rows per thread
-constexpr int kSolveWarps = 4;   // warps per solve block (batched kernels)
 constexpr int kRounds = 1;       // system batches per warp (one: more, shorter blocks balance best)
 constexpr int kBwdLook = 2;      // back-sweep pipeline depth (see bwd_step)
 // The grid and point-list solve kernels run 8-warp blocks, 2 per SM (the same
@@ -353,7 +352,7 @@ __device__ __forceinline__ int exp_above(float v) { return ((__float_as_int(v) >
 // With kIdw the block also writes the IDW depth over the first fz.k of the
 // node's sorted neighbours (fz.k <= k): the same value bg_interp_idw gives, as
 // its operations are those of idw_from in the same order.
-template <int K, bool kPts = false, bool kIdw = false, int kWarps = kSolveWarps>
+template <int K, bool kPts, bool kIdw, int kWarps>
 __device__ __forceinline__ void okrige_solve_block(const HashView& h, const GridView& g, int k,
                                                    const OkParams& p, int64_t node0, int64_t nodes,
                                                    const int32_t* __restrict__ ids,

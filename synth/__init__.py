@@ -24,7 +24,7 @@ import math
 import numpy as np
 
 __all__ = [
-    "GridSpec", "Workload", "HoleGrid", "bumps", "seafloor", "to_cm", "tile", "swath",
+    "GridSpec", "Workload", "HoleGrid", "bumps", "seafloor", "to_cm", "tile", "rect", "swath",
     "batched_tiles", "hole_grid", "row_midpoints", "random_points",
 ]
 
@@ -154,6 +154,22 @@ def tile(seed: int = 1, n: int = 20_000, side_cm: int = 51_200, cell_cm: int = 2
     grid = GridSpec(x0_cm, y0_cm, cell_cm, nx, nx)
     return Workload(x.astype(np.int32), y.astype(np.int32), z.astype(np.float32), grid,
                     f"tile{n}", dict(seed=seed, n=n, side_cm=side_cm, cell_cm=cell_cm))
+
+
+def rect(seed: int, n: int, x0_cm: int, y0_cm: int, w_cm: int, h_cm: int, grid: GridSpec,
+         n_bumps: int = 40) -> Workload:
+    """Uniform soundings over the rectangle [x0, x0+w) x [y0, y0+h) cm with
+    the seafloor model (n_bumps bumps over the rectangle), gridded on `grid`.
+    Long thin rectangles give the extreme aspect ratios that stress a hash's
+    cell-size choice."""
+    rng = _rng(seed)
+    x = rng.integers(0, w_cm, n, dtype=np.int64) + x0_cm
+    y = rng.integers(0, h_cm, n, dtype=np.int64) + y0_cm
+    table = bumps(rng, x0_cm / 100.0, (x0_cm + w_cm) / 100.0,
+                  y0_cm / 100.0, (y0_cm + h_cm) / 100.0, count=n_bumps)
+    z = seafloor(x / 100.0, y / 100.0, table, rng)
+    return Workload(x.astype(np.int32), y.astype(np.int32), z.astype(np.float32), grid, "rect",
+                    dict(seed=seed, n=n, x0_cm=x0_cm, y0_cm=y0_cm, w_cm=w_cm, h_cm=h_cm))
 
 
 def swath(seed: int = 2, lines: int = 4, pings: int = 20_000, beams: int = 256,

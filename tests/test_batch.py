@@ -15,15 +15,22 @@ pytestmark = pytest.mark.gpu
 VGM = (0, 0.25, 100.0, 50.0)
 
 
-def _mk(bg, torch, tiles_np):
+# k per tile, cycled by tile index: every batched system size (K = 4, 8, 16,
+# 32 for kriging; the IDW k-NN at K = 4, 8, 16) and k below its K
+IDW_KS = (16, 4, 8, 12)
+OK_KS = (32, 4, 8, 16, 5, 24)
+
+
+def _mk(bg, torch, tiles_np, cycle_k=False):
     dev = torch.device("cuda:0")
     tiles = []
-    for w, m in tiles_np:
+    for i, (w, m) in enumerate(tiles_np):
         g = w.grid
         t = dict(x_cm=torch.from_numpy(w.x_cm).to(dev), y_cm=torch.from_numpy(w.y_cm).to(dev),
                  z_m=torch.from_numpy(w.z_m).to(dev),
                  grid_spec=(g.x0_cm, g.y0_cm, g.cell_cm, g.nx, g.ny), method=m,
-                 k=16 if m == 0 else 32, power=2.0, vgm=bg.variogram(*VGM),
+                 k=(IDW_KS[i % len(IDW_KS)] if m == 0 else OK_KS[i % len(OK_KS)]) if cycle_k
+                 else (16 if m == 0 else 32), power=2.0, vgm=bg.variogram(*VGM),
                  depth_out=torch.full((g.m,), -1.0, device=dev),
                  var_out=torch.full((g.m,), -1.0, device=dev) if m == 1 else None)
         tiles.append(t)
@@ -57,7 +64,9 @@ def test_batch_equals_per_grid_calls_and_replays():
     tiles_np = synth.batched_tiles(seed=3, count=24, scale=0.05)
     ctx = bg.ctx_create(0)
     try:
-        tiles = _mk(bg, torch, tiles_np)
+        tiles = _mk(bg, torch, tiles_np, cycle_k=True)
+        used = {(t["method"], t["k"]) for t in tiles}
+        assert {(1, 4), (1, 8), (1, 16), (1, 32), (0, 4), (0, 8), (0, 16)} <= used
         ref = [_direct(bg, torch, ctx, t) for t in tiles]
         b = bg.batch_create(ctx, tiles)
         for run in range(3):  # capture, then replays

@@ -74,6 +74,58 @@ def test_knn_matches_python_sort(seed):
             assert np.all(idx[q, keff[q]:] == -1)
 
 
+@pytest.mark.parametrize("seed", range(8))
+def test_tree_knn_equals_brute_force(seed):
+    # the 2-d tree must return the brute force's (d2, index) lists exactly: ties,
+    # duplicate positions, NaN depths, N < k, and spans from a few cm to km
+    rng = np.random.default_rng(100 + seed)
+    n = int(rng.choice([1, 7, 9, 40, 300, 5000]))
+    span = int(rng.choice([3, 50, 4000, 10**8]))
+    x = rng.integers(-span, span, n).astype(np.int32)
+    y = rng.integers(-span, span, n).astype(np.int32)
+    if seed % 2:
+        x[: n // 3] = x[0]  # a column of equal x (median splits through equal keys)
+    z = rng.normal(size=n).astype(np.float32)
+    z[rng.random(n) < 0.15] = np.nan
+    m = 300
+    qx = rng.integers(-span - 5, span + 5, m).astype(np.int32)
+    qy = rng.integers(-span - 5, span + 5, m).astype(np.int32)
+    tree = oracle.Tree(x, y, z)
+    for k in (1, 4, 16, 33):
+        ref = oracle.knn(x, y, z, qx, qy, k, nthreads=2)
+        got = oracle.knn(x, y, z, qx, qy, k, nthreads=2, tree=tree)
+        for a, b in zip(ref, got):
+            assert np.array_equal(a, b)
+
+
+def test_tree_knn_lattice_duplicates_and_empty():
+    xs, ys = np.meshgrid(np.arange(40) * 100, np.arange(30) * 100)
+    x = np.concatenate([xs.ravel(), xs.ravel()[::7]]).astype(np.int32)  # every 7th point twice
+    y = np.concatenate([ys.ravel(), ys.ravel()[::7]]).astype(np.int32)
+    z = np.arange(x.size, dtype=np.float32)
+    qx, qy = oracle.grid_nodes(-150, -150, 100, 44, 34)  # nodes on cell centres, ties everywhere
+    qx = np.concatenate([qx, x[::13]])                    # and nodes on soundings
+    qy = np.concatenate([qy, y[::13]])
+    tree = oracle.Tree(x, y, z)
+    for k in (4, 8, 32):
+        ref = oracle.knn(x, y, z, qx, qy, k)
+        got = oracle.knn(x, y, z, qx, qy, k, tree=tree)
+        assert all(np.array_equal(a, b) for a, b in zip(ref, got))
+        # IDW and kriging take the same neighbours, so the same values bit for bit
+        assert np.array_equal(oracle.idw(x, y, z, qx, qy, k, tree=tree), oracle.idw(x, y, z, qx, qy, k))
+        a = oracle.okrige(x, y, z, qx[:200], qy[:200], k, tree=tree)
+        b = oracle.okrige(x, y, z, qx[:200], qy[:200], k)
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    # no valid sounding, and no sounding at all
+    for xx, yy, zz in ((x[:5], y[:5], np.full(5, np.nan, np.float32)),
+                       (x[:0], y[:0], z[:0])):
+        t = oracle.Tree(xx, yy, zz)
+        idx, d2, keff = oracle.knn(xx, yy, zz, qx[:10], qy[:10], 4, tree=t)
+        assert (keff == 0).all() and (idx == -1).all() and (d2 == -1).all()
+    with pytest.raises(ValueError):
+        oracle.knn(x[:-1], y[:-1], z[:-1], qx, qy, 4, tree=tree)  # built from other soundings
+
+
 def test_knn_lattice_ties_break_by_index():
     # node at the centre of a 2 x 2 cell of a unit lattice: four soundings tie at every ring
     xs, ys = np.meshgrid(np.arange(6) * 100, np.arange(6) * 100)
@@ -277,6 +329,49 @@ def test_okrige_k2_hand_worked():
     mu_ref = g(2) - g(10) * (1 - c["expected"])
     assert mu[0] == pytest.approx(mu_ref, abs=1e-10)
     assert v[0] == pytest.approx(c["expected"] * g(2) + (1 - c["expected"]) * g(8) + mu_ref, abs=1e-10)
+
+
+def _ok_golden(name):
+    c = _golden()[name]
+    x, y, z = _arrays(c["pts"])
+    p = c["params"]
+    d, v, lam, mu, idx = oracle.okrige(x, y, z, [c["node"][0]], [c["node"][1]], int(p["k"]),
+                                       int(p["model"]), p["nugget"], p["sill"], p["range"],
+                                       want_weights=True, want_idx=True)
+    return c, z, d[0], v[0], lam[0], mu[0], idx[0]
+
+
+def test_okrige_colocated_pair_hand_worked():
+    # two distinct soundings at one position take gamma = c0 (the h -> 0+ limit)
+    c, z, d, v, lam, mu, idx = _ok_golden("ok_dup_k2_mu")
+    assert list(idx) == [0, 1]
+    assert np.allclose(lam, 0.5, atol=1e-13)
+    assert d == pytest.approx(15.0, abs=1e-12)
+    assert mu == pytest.approx(c["expected"], abs=1e-12)
+    assert v == pytest.approx(_golden()["ok_dup_k2_var"]["expected"], abs=1e-12)
+
+
+def test_okrige_colocated_pair_with_third_sounding_hand_worked():
+    c, z, d, v, lam, mu, idx = _ok_golden("ok_dup_k3_lambda")
+    a = c["expected"]
+    assert list(idx) == [0, 1, 2]
+    assert lam[0] == pytest.approx(a, abs=1e-13) and lam[1] == pytest.approx(a, abs=1e-13)
+    assert lam[2] == pytest.approx(1 - 2 * a, abs=1e-13)
+    assert d == pytest.approx(10 * a + 20 * a + 40 * (1 - 2 * a), abs=1e-11)
+    assert mu == pytest.approx(_golden()["ok_dup_k3_mu"]["expected"], abs=1e-11)
+    assert v == pytest.approx(_golden()["ok_dup_k3_var"]["expected"], abs=1e-11)
+
+
+def test_okrige_node_on_colocated_pair_hand_worked():
+    # the node on P: gamma_0 = 0 to P and P', but P and P' take c0 to each other
+    c, z, d, v, lam, mu, idx = _ok_golden("ok_dup_node_lambda3")
+    l3 = c["expected"]
+    assert list(idx) == [0, 1, 2]
+    assert lam[0] == pytest.approx((1 - l3) / 2, abs=1e-13)
+    assert lam[1] == pytest.approx((1 - l3) / 2, abs=1e-13)
+    assert lam[2] == pytest.approx(l3, abs=1e-13)
+    assert d == pytest.approx(15 * (1 - l3) + 40 * l3, abs=1e-11)
+    assert v == pytest.approx(_golden()["ok_dup_node_var"]["expected"], abs=1e-12)
 
 
 def test_okrige_k2_general_closed_form():

@@ -1,9 +1,12 @@
 """Parity at the benchmark's full size: the 4-line survey swath (20.48M
 soundings, 20,000 x 3,692 nodes at 0.5 m), IDW k=16 and kriging k=32, in the
 launch configuration bench.py times. The GPU grids every node; the oracle
-recomputes a sample of nodes one by one (swath interior, swath edges, the
-inter-line gaps and the grid border) by brute force.
+recomputes about 290,000 of them one by one (200,000 anywhere, every node of
+the grid's border, nodes along the edges of each survey line's coverage and
+in the gaps between lines), with its 2-d tree k-NN over all 20.48M soundings.
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -27,12 +30,23 @@ def swath_run():
     x, y, z = (torch.from_numpy(a).to(dev) for a in (w.x_cm, w.y_cm, w.z_m))
     s = bg.soundings_upload(ctx, x, y, z)
     rng = np.random.default_rng(11)
-    sel = np.concatenate([
-        rng.choice(g.m, 300, replace=False),                         # anywhere
-        np.arange(0, g.nx, 997),                                     # first row (grid border)
-        (g.ny - 1) * g.nx + np.arange(3, g.nx, 1009),                # last row
-        rng.integers(0, g.nx, 60) + g.nx * rng.integers(700, 1000, 60),   # gap between lines 1 and 2
-    ]).astype(np.int64)
+    # survey geometry of the generator: line l covers y in [500 l, 500 l + 346.4] m
+    spacing_m, width_m = w.params["line_spacing_m"], 2 * 100.0 * math.tan(math.radians(60.0))
+    rows_per_m = 100.0 / g.cell_cm
+    edge_rows = [int(round((spacing_m * l + e) * rows_per_m)) + dj
+                 for l in range(w.params["lines"]) for e in (0.0, width_m) for dj in (-2, 0, 2)]
+    edge_rows = [j for j in edge_rows if 0 <= j < g.ny]
+    gap_lo, gap_hi = int((width_m + 2) * rows_per_m), int((spacing_m - 2) * rows_per_m)
+    sel = np.unique(np.concatenate([
+        rng.choice(g.m, 200_000, replace=False),                     # anywhere
+        np.arange(g.nx),                                              # first row (grid border)
+        (g.ny - 1) * g.nx + np.arange(g.nx),                          # last row
+        np.arange(g.ny) * g.nx, np.arange(g.ny) * g.nx + g.nx - 1,    # first and last columns
+        (rng.integers(0, g.nx, (len(edge_rows), 1500))
+         + g.nx * np.array(edge_rows)[:, None]).ravel(),              # along the coverage edges
+        rng.integers(0, g.nx, 20_000) + g.nx * rng.integers(gap_lo, gap_hi, 20_000),  # gaps
+    ]).astype(np.int64))
+    assert sel.size >= 250_000
     sel_t = torch.from_numpy(sel).to(dev)
     out = {}
     d = torch.empty(g.m, device=dev)
@@ -83,6 +97,7 @@ def swath_run():
     bg.ctx_destroy(ctx)
     qx = (g.x0_cm + (sel % g.nx) * g.cell_cm + g.cell_cm // 2).astype(np.int32)
     qy = (g.y0_cm + (sel // g.nx) * g.cell_cm + g.cell_cm // 2).astype(np.int32)
+    out["tree"] = oracle.Tree(w.x_cm, w.y_cm, w.z_m)
     return w, qx, qy, out
 
 
@@ -90,7 +105,7 @@ def test_swath_idw_k16(swath_run):
     w, qx, qy, out = swath_run
     d, nb, n_nan = out["idw"]
     assert n_nan == 0
-    ref, ridx = oracle.idw(w.x_cm, w.y_cm, w.z_m, qx, qy, 16, 2.0, want_idx=True)
+    ref, ridx = oracle.idw(w.x_cm, w.y_cm, w.z_m, qx, qy, 16, 2.0, want_idx=True, tree=out["tree"])
     assert np.array_equal(nb, ridx)
     assert_idw(d, ref)
 
@@ -100,7 +115,7 @@ def test_swath_okrige_k32(swath_run):
     d, v, nb, n_nan, vmin = out["ok"]
     assert n_nan == 0 and vmin >= -1e-3
     rd, rv, ridx = oracle.okrige(w.x_cm, w.y_cm, w.z_m, qx, qy, 32, 0, 0.25, 100.0, 50.0,
-                                 want_idx=True)
+                                 want_idx=True, tree=out["tree"])
     assert np.array_equal(nb, ridx)
     assert_okrige(d, v, rd, rv, 0.25)
 
