@@ -43,11 +43,22 @@ IDW_K, IDW_P = 16, 2.0
 OK_K = 32
 VGM = (0, 0.25, 100.0, 50.0)  # spherical, nugget 0.25 m^2, total sill 100 m^2, range 50 m
 
-# Algorithmic work per node of the kriging kernel at k = 32 (reduced system of
-# n = 31 unknowns), FP32 flops (an FMA counts 2): Cholesky n^3/3, two solves
-# (solution + refinement correction) of 2 n^2 each, assembly of n(n+1)/2
-# variogram entries at ~12 flops (dx^2+dy^2, sqrt, scale, cubic) plus the
-# n^2 matrix fill (2 flops). The FP64 residual (n^2 FMA) is counted apart.
+# Algorithmic work per grid node, the per-unit figures of the roofline:
+#  - kriging k = 32 (the contract's model): about 35,000 FP32 flops per node
+#    (LU of the bordered (k+1) x (k+1) system, its solves and the variogram
+#    assembly), plus the FP64 residual counted apart;
+#  - the solver's own count for the reduced system of n = k - 1 unknowns: Cholesky
+#    n^3/3, two solves (solution + refinement correction) of 2 n^2 each, assembly
+#    of n(n+1)/2 + n variogram entries at ~12 flops plus the n^2 matrix fill;
+#  - exact k-NN: about 9k/pi candidates per node (cell side ~ the k-th
+#    distance), 8 integer operations each (2 subtractions, 2 multiplies, an
+#    add, compare and select), so 733 at k = 32 and 367 at k = 16;
+#  - HBM bytes: the hash build reads 8 + 12 and writes 16 bytes per sounding;
+#    the k-NN ids kernel writes 4 k bytes per node; the IDW kernel reads each
+#    16-byte record once and writes 4 bytes per node.
+OK_FLOPS_PER_NODE_MODEL = 35_000.0
+
+
 def okrige_flops_per_node(k=OK_K):
     n = k - 1
     chol = n ** 3 / 3.0
@@ -56,20 +67,17 @@ def okrige_flops_per_node(k=OK_K):
     return chol + solves + assembly
 
 
-def okrige_fp64_flops_per_node(k=OK_K):
-    n = k - 1
-    return 2 * n * n
+def knn_int_ops_per_node(k):
+    return 9.0 * k / 3.141592653589793 * 8.0
 
+
+HASH_BYTES_PER_SOUNDING = 36.0
 
 # DRAM bytes (read + write) per node of k_okrige_solve<32> with the fused IDW,
 # from one ncu capture of the current kernel on the 2-line swath (3.384M
 # nodes: 450.4 MB read + 38.3 MB written per launch, mostly the 128 B of
 # neighbour ids per node); traffic grows with the nodes of a launch.
 SOLVE_DRAM_BYTES_PER_NODE = (452.216064e6 + 38.499584e6) / 3.384e6
-
-# FP32 peak for "alu"-bound roofline: 152 SMs x 128 FP32 lanes x 2 flops/FMA x
-# the maximum SM clock (2,070 MHz) = 80.5 TFLOP/s.
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 
 
 def load_peaks():
@@ -152,37 +160,95 @@ class ClockSampler:
 # -------------------------------------------------------------- CPU oracle
 
 def oracle_sample(w, nodes: int, seed: int = 0):
+    """Node indices and coordinates of `nodes` distinct random grid nodes."""
     g = w.grid
     rng = np.random.default_rng(seed)
-    sel = rng.choice(g.m, nodes, replace=False)
+    sel = np.sort(rng.choice(g.m, min(nodes, g.m), replace=False))
     qx = (g.x0_cm + (sel % g.nx) * g.cell_cm + g.cell_cm // 2).astype(np.int32)
     qy = (g.y0_cm + (sel // g.nx) * g.cell_cm + g.cell_cm // 2).astype(np.int32)
-    return qx, qy
+    return sel, qx, qy
 
 
-def run_oracle(w, qx, qy):
+def run_oracle(w, qx, qy, tree, nthreads=0):
+    """FP64 IDW k=16 and kriging k=32 of the step at the given nodes."""
     import oracle
-    oracle.idw(w.x_cm, w.y_cm, w.z_m, qx, qy, IDW_K, IDW_P)
-    oracle.okrige(w.x_cm, w.y_cm, w.z_m, qx, qy, OK_K, *VGM)
+    ri = oracle.idw(w.x_cm, w.y_cm, w.z_m, qx, qy, IDW_K, IDW_P, nthreads=nthreads, tree=tree)
+    rd, rv = oracle.okrige(w.x_cm, w.y_cm, w.z_m, qx, qy, OK_K, *VGM, nthreads=nthreads,
+                           tree=tree)
+    return ri, rd, rv
+
+
+def oracle_timing(w, nodes, nthreads, seed):
+    """Seconds to build the oracle's 2-d tree and per node for IDW + kriging."""
+    import oracle
+    t0 = time.perf_counter()
+    tree = oracle.Tree(w.x_cm, w.y_cm, w.z_m, nthreads=nthreads)
+    t_build = time.perf_counter() - t0
+    _, qx, qy = oracle_sample(w, nodes, seed)
+    t0 = time.perf_counter()
+    run_oracle(w, qx, qy, tree, nthreads)
+    t_query = time.perf_counter() - t0
+    tree.close()
+    return t_build, t_query / qx.size, qx.size
 
 
 def cpu_baseline(w, target_s: float = 15.0):
-    """Time the FP64 oracle on a bounded sample of nodes (~target_s of CPU work)."""
+    """The FP64 oracle as it stands (2-d tree k-NN, IDW, kriging by Gaussian
+    elimination) on the host cores: the tree is built over all soundings and a
+    bounded sample of nodes is gridded (about target_s of CPU work); the
+    whole-grid rate is projected as nodes / (build + nodes x time per node).
+    Also the same on one thread (smaller sample)."""
     import oracle
     cores = oracle.threads()
-    qx, qy = oracle_sample(w, max(cores, 8), seed=99)
-    t0 = time.perf_counter()
-    run_oracle(w, qx, qy)
-    per_node = (time.perf_counter() - t0) / qx.size
-    n = int(max(cores, min(200_000, target_s / max(per_node, 1e-9))))
-    qx, qy = oracle_sample(w, n, seed=7)
-    t0 = time.perf_counter()
-    run_oracle(w, qx, qy)
-    dt = time.perf_counter() - t0
-    return {"value": n / dt, "unit": "nodes/s", "cores": cores, "kind": "oracle",
-            "sample": f"{n} random nodes of the {w.grid.nx}x{w.grid.ny} swath grid, brute-force "
-                      f"exact k-NN over all {w.x_cm.size} soundings, FP64 IDW k={IDW_K} + "
-                      f"kriging k={OK_K} per node ({dt:.1f} s)"}
+    _, per0, _ = oracle_timing(w, 2000, 0, seed=98)
+    n = int(min(w.grid.m, max(4 * cores, target_s * 0.7 / max(per0, 1e-9))))
+    t_build, per, n = oracle_timing(w, n, 0, seed=7)
+    value = w.grid.m / (t_build + w.grid.m * per)
+    n1 = int(min(w.grid.m, max(16, target_s * 0.2 / max(per0 * cores, 1e-9))))
+    t_build1, per1, n1 = oracle_timing(w, n1, 1, seed=8)
+    return {"value": value, "unit": "nodes/s", "cores": cores, "kind": "oracle",
+            "sample": f"2-d tree over all {w.x_cm.size} soundings ({t_build:.2f} s on {cores} "
+                      f"threads), then FP64 IDW k={IDW_K} + kriging k={OK_K} at {n} random nodes "
+                      f"of the {w.grid.nx}x{w.grid.ny} swath grid ({per * 1e6:.2f} us per node); "
+                      f"value = whole grid projected: nodes / (build + nodes x per-node time)",
+            "nodes_per_s_queries_only": 1.0 / per,
+            "single_thread": {"value": w.grid.m / (t_build1 + w.grid.m * per1), "unit": "nodes/s",
+                              "tree_build_s": t_build1, "nodes": n1,
+                              "nodes_per_s_queries_only": 1.0 / per1}}
+
+
+def error_stats(got, ref, tol, nan_ref=None):
+    """max / p99 |got - ref| and the counts over tol on finite reference values."""
+    got = np.asarray(got, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    ok = ~np.isnan(ref)
+    e = np.abs(got[ok] - ref[ok])
+    t = tol[ok] if np.ndim(tol) else tol
+    return {"nodes": int(ok.sum()), "max": float(e.max()) if e.size else 0.0,
+            "p99": float(np.percentile(e, 99)) if e.size else 0.0,
+            "over_tol": int((e > t).sum()), "nan_mismatch": int((np.isnan(got) != ~ok).sum())}
+
+
+def half_ulp32(v):
+    return 0.5 * np.spacing(np.abs(np.asarray(v, np.float64)).astype(np.float32)).astype(np.float64)
+
+
+def compare_with_oracle(idw, depth, var, ri, rd, rv, nugget=VGM[1]):
+    """Per-result error of the GPU grids against the FP64 oracle (tolerances:
+    IDW 1e-4 m + half an fp32 ulp; kriging depth 1e-3 m; variance
+    1e-4 sigma^2 + 1e-4 nugget)."""
+    out = {}
+    if idw is not None:
+        out["idw_depth_m"] = error_stats(idw, ri, 1e-4 + half_ulp32(ri))
+        out["idw_depth_m"]["over_1e-4"] = int((np.abs(np.asarray(idw, np.float64) - ri) > 1e-4).sum())
+    if depth is not None:
+        out["kriging_depth_m"] = error_stats(depth, rd, 1e-3)
+    if var is not None:
+        out["kriging_variance_m2"] = error_stats(var, rv, 1e-4 * np.abs(rv) + 1e-4 * nugget)
+        r = np.abs(np.asarray(var, np.float64) - rv) / np.maximum(np.abs(rv), 1e-30)
+        r = r[~np.isnan(rv)]
+        out["kriging_variance_m2"]["max_rel"] = float(r.max()) if r.size else 0.0
+    return out
 
 
 # ------------------------------------------------------------------- main
@@ -279,7 +345,7 @@ def serving_measure(bg, torch, ctx, pool, rate, n_tiles, seed):
     return {"rate_per_s": rate, "tiles": n_tiles, "serving": serve, "plain": plain}
 
 
-def batched_measure(bg, torch, ctx, pool, n_tiles, steps):
+def batched_measure(bg, torch, ctx, pool, n_tiles, steps, check_nodes_per_tile=256):
     """A batch of n_tiles tiles (drawn cyclically from the pool) in one graph of
     persistent kernels, against the same tiles gridded one per-grid call
     sequence after another. Inputs and outputs stay in device memory."""
@@ -310,6 +376,8 @@ def batched_measure(bg, torch, ctx, pool, n_tiles, steps):
     ms = e0.elapsed_time(e1) / steps
     status = bg.batch_status(b)
     bg.batch_destroy(b)
+    check = (oracle_check_batch(torch, tiles, pool, n_tiles, check_nodes_per_tile)
+             if check_nodes_per_tile else None)
     # the same tiles, one per-grid call sequence each
     torch.cuda.synchronize()
     e0.record()
@@ -328,7 +396,44 @@ def batched_measure(bg, torch, ctx, pool, n_tiles, steps):
     return {"tiles": n_tiles, "distinct_tiles": len(pool), "nodes": int(nodes),
             "ms_per_batch": ms, "nodes_per_s": nodes / (ms / 1e3),
             "per_tile_calls_ms": per_tile_ms, "per_tile_calls_nodes_per_s": nodes / (per_tile_ms / 1e3),
-            "cell_target_tuned": best, "status_flags": status}
+            "cell_target_tuned": best, "status_flags": status, "errors_vs_oracle": check}
+
+
+def oracle_check_batch(torch, tiles, pool, n_tiles, per_tile=256, seed=5):
+    """Error of every tile of the timed batch against the FP64 oracle at
+    `per_tile` random nodes per tile (one 2-d tree per distinct tile)."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    trees = {}
+    acc = {0: ([], []), 1: ([], [], [], [], [])}
+    for i in range(n_tiles):
+        w, m = pool[i % len(pool)]
+        t = tiles[i]
+        g = w.grid
+        sel = np.sort(rng.choice(g.m, min(per_tile, g.m), replace=False))
+        qx = (g.x0_cm + (sel % g.nx) * g.cell_cm + g.cell_cm // 2).astype(np.int32)
+        qy = (g.y0_cm + (sel // g.nx) * g.cell_cm + g.cell_cm // 2).astype(np.int32)
+        tr = trees.get(i % len(pool))
+        if tr is None:
+            tr = trees[i % len(pool)] = oracle.Tree(w.x_cm, w.y_cm, w.z_m)
+        st = torch.from_numpy(sel).to(t["depth_out"].device)
+        got = t["depth_out"][st].cpu().numpy()
+        if m == 0:
+            acc[0][0].append(got)
+            acc[0][1].append(oracle.idw(w.x_cm, w.y_cm, w.z_m, qx, qy, t["k"], IDW_P, tree=tr))
+        else:
+            rd, rv = oracle.okrige(w.x_cm, w.y_cm, w.z_m, qx, qy, t["k"], *VGM, tree=tr)
+            acc[1][0].append(got)
+            acc[1][1].append(t["var_out"][st].cpu().numpy())
+            acc[1][2].append(rd)
+            acc[1][3].append(rv)
+    for tr in trees.values():
+        tr.close()
+    cat = lambda a: np.concatenate(a) if a else np.zeros(0)
+    out = compare_with_oracle(cat(acc[0][0]), cat(acc[1][0]), cat(acc[1][1]), cat(acc[0][1]),
+                              cat(acc[1][2]), cat(acc[1][3]))
+    out["sample"] = f"{per_tile} random nodes of each of the {n_tiles} tiles"
+    return out
 
 
 def gridded_measure(bg, torch, n_side, fracs, steps=5):
@@ -460,30 +565,36 @@ def dist_env():
 
 
 def bench_reference(args):
+    """The FP64 oracle on the host cores. One step = build the 2-d tree over
+    all soundings, then IDW + kriging at a bounded sample of grid nodes
+    (--ref-nodes); value = the whole grid projected from the steps' build and
+    per-node times (nodes / (build + nodes x per-node time))."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return
     w = workload(args)
     import oracle
     cores = oracle.threads()
-    per_step_nodes = max(cores, int(args.ref_nodes))
+    nodes = max(cores, int(args.ref_nodes))
     for i in range(args.warmup):
-        qx, qy = oracle_sample(w, min(per_step_nodes, cores), seed=1000 + i)
-        run_oracle(w, qx, qy)
-    times = []
+        oracle_timing(w, min(nodes, 4 * cores), 0, seed=1000 + i)
+    builds, pers, walls = [], [], []
     for i in range(args.steps):
-        qx, qy = oracle_sample(w, per_step_nodes, seed=i)
         t0 = time.perf_counter()
-        run_oracle(w, qx, qy)
-        times.append(time.perf_counter() - t0)
-    total = sum(times)
-    value = per_step_nodes * args.steps / total
-    sample = (f"{per_step_nodes} random nodes per step of the {w.grid.nx}x{w.grid.ny} swath grid; "
-              f"brute-force exact k-NN over {w.x_cm.size} soundings, FP64 IDW k={IDW_K} + kriging "
-              f"k={OK_K}")
+        t_build, per, n = oracle_timing(w, nodes, 0, seed=i)
+        walls.append(time.perf_counter() - t0)
+        builds.append(t_build)
+        pers.append(per)
+    t_build = statistics.mean(builds)
+    per = statistics.mean(pers)
+    value = w.grid.m / (t_build + w.grid.m * per)
+    sample = (f"per step: 2-d tree over all {w.x_cm.size} soundings ({t_build:.2f} s), then FP64 "
+              f"IDW k={IDW_K} + kriging k={OK_K} at {nodes} random nodes of the "
+              f"{w.grid.nx}x{w.grid.ny} swath grid ({per * 1e6:.2f} us per node on {cores} "
+              f"threads); value = whole grid projected: nodes / (build + nodes x per-node time)")
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "nodes/s",
            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-           "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+           "ms_per_step": 1e3 * statistics.mean(walls), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": config_dict(w, args),
            "cpu_baseline": {"value": value, "unit": "nodes/s", "cores": cores, "kind": "oracle",
@@ -504,6 +615,176 @@ def config_dict(w, args):
                         "range_m": VGM[3]},
             "seed": w.params["seed"], "l2": "inputs and outputs larger than L2 (no flush)",
             "parallelism": f"replica x{args.gpus}"}
+
+
+def measure_alu_peaks(bg, device):
+    """FP32 FMA, INT32 (multiply-add; add + xor) and FP64 FMA rates of this
+    GPU from the library's own microbenchmark, with the SM clock each kernel
+    ran at and the rate per SM per cycle (so that a kernel timed at another
+    clock is compared at its own)."""
+    import torch
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    out = {"sms": sms}
+    for kind in bg.ALU_KINDS:
+        ops, mhz = bg.alu_peak(kind, device)
+        out[kind] = {"ops_per_s": ops, "sm_mhz": mhz,
+                     "ops_per_sm_cycle": ops / (sms * mhz * 1e6) if mhz > 0 else None}
+    return out
+
+
+def _alu_peak_at(peaks, kind, mhz):
+    per = peaks[kind]["ops_per_sm_cycle"]
+    return per * peaks["sms"] * mhz * 1e6 if per else peaks[kind]["ops_per_s"]
+
+
+def rooflines(prof, sep_prof, peaks, mpeaks, step_mhz, sms, w, steps, sep_mhz):
+    """One roofline entry per hot kernel. ALU peaks are the measured rates per
+    SM cycle at the median SM clock sampled while the kernel's step ran; the
+    HBM peak is the measured copy bandwidth (MEASURED_PEAKS.json)."""
+    hbm = mpeaks.get("hbm_gbs")
+    hbm_src = "measured" if hbm else "fallback"
+    hbm = hbm or 6800.0
+    fp32 = _alu_peak_at(peaks, "fp32_fma", step_mhz) / 1e12
+    int32 = max(_alu_peak_at(peaks, "int32_imad", step_mhz),
+                _alu_peak_at(peaks, "int32_add_xor", step_mhz)) / 1e12
+    out = {}
+    # kriging solve (k = 32, fused IDW k = 16): the dominant kernel
+    s_ms, s_launch, s_nodes = prof["kriging_solve"]
+    avg = s_ms / max(s_launch, 1)
+    npl = s_nodes / max(s_launch, 1)
+    ach = OK_FLOPS_PER_NODE_MODEL * npl / (avg / 1e3) / 1e12
+    own = okrige_flops_per_node() * npl / (avg / 1e3) / 1e12
+    out["kriging_solve"] = {
+        "bound": "alu", "kernel": "k_okrige_solve<32> (kriging k=32 solve, fused IDW k=16)",
+        "achieved": ach, "peak": fp32, "unit": "TFLOP/s", "frac": ach / fp32,
+        "traffic": SOLVE_DRAM_BYTES_PER_NODE * npl,
+        "flops_per_node": OK_FLOPS_PER_NODE_MODEL, "flops_model": "35k FP32 flops per node",
+        "own_count": {"flops_per_node": okrige_flops_per_node(), "achieved": own,
+                      "frac": own / fp32},
+        "avg_launch_ms": avg, "nodes_per_launch": npl, "launches_per_step": s_launch / steps,
+        "peak_source": f"measured FP32 FMA rate per SM cycle x {sms} SMs x {step_mhz:.0f} MHz "
+                       "(median SM clock of the timed steps)",
+        "traffic_source": "ncu dram bytes of the same kernel on a 3.384M-node swath, scaled "
+                          "per node",
+        "hbm_frac": SOLVE_DRAM_BYTES_PER_NODE * npl / (avg / 1e3) / 1e9 / hbm}
+    # k-NN ids (k = 32) of the kriging pass
+    k_ms, k_launch, k_nodes = prof["kriging_knn_ids"]
+    avg = k_ms / max(k_launch, 1)
+    npl = k_nodes / max(k_launch, 1)
+    ach = knn_int_ops_per_node(OK_K) * npl / (avg / 1e3) / 1e12
+    byt = 4.0 * OK_K * npl
+    out["knn_ids_k32"] = {
+        "bound": "alu", "kernel": "k_knn_ids<32>", "achieved": ach, "peak": int32,
+        "unit": "Tops/s (INT32)", "frac": ach / int32,
+        "int_ops_per_node": knn_int_ops_per_node(OK_K), "avg_launch_ms": avg,
+        "nodes_per_launch": npl, "hbm_gbs": byt / (avg / 1e3) / 1e9,
+        "hbm_frac": byt / (avg / 1e3) / 1e9 / hbm, "bytes_per_node": 4.0 * OK_K,
+        "peak_source": "measured INT32 rate (larger of multiply-add and add/xor) per SM cycle "
+                       f"x {sms} SMs x {step_mhz:.0f} MHz"}
+    # IDW k = 16 on its own (the separate-calls step): k-NN + weights in one kernel
+    i_ms, i_launch, i_nodes = sep_prof["idw"]
+    if i_launch:
+        int32s = max(_alu_peak_at(peaks, "int32_imad", sep_mhz),
+                     _alu_peak_at(peaks, "int32_add_xor", sep_mhz)) / 1e12
+        avg = i_ms / i_launch
+        npl = i_nodes / i_launch
+        nval = int(np.count_nonzero(~np.isnan(w.z_m)))
+        byt = (16.0 * nval) / i_launch + 4.0 * npl
+        ach = knn_int_ops_per_node(IDW_K) * npl / (avg / 1e3) / 1e12
+        out["idw_k16"] = {
+            "bound": "alu", "kernel": "k_idw<16>", "achieved": ach, "peak": int32s,
+            "unit": "Tops/s (INT32)", "frac": ach / int32s,
+            "int_ops_per_node": knn_int_ops_per_node(IDW_K),
+            "hbm": {"bytes_per_launch": byt, "achieved_gbs": byt / (avg / 1e3) / 1e9,
+                    "peak_gbs": hbm, "frac": byt / (avg / 1e3) / 1e9 / hbm,
+                    "peak_source": hbm_src},
+            "avg_launch_ms": avg, "nodes_per_launch": npl,
+            "note": "the HBM fraction is far below 0.5: the k-NN's integer work per node, "
+                    "not bytes, bounds IDW"}
+    return out
+
+
+def oracle_check_swath(w, torch, d_idw, d_ok, v_ok, nodes):
+    """Error of the step's three grids against the FP64 oracle (2-d tree) at
+    `nodes` random nodes plus every node of two rows in the gap between
+    survey lines."""
+    import oracle
+    g = w.grid
+    sel, _, _ = oracle_sample(w, nodes, seed=2024)
+    gap = np.arange(g.nx) + g.nx * 850  # a row in the gap between lines 1 and 2
+    sel = np.unique(np.concatenate([sel, gap, gap + g.nx * 1000]))
+    qx = (g.x0_cm + (sel % g.nx) * g.cell_cm + g.cell_cm // 2).astype(np.int32)
+    qy = (g.y0_cm + (sel // g.nx) * g.cell_cm + g.cell_cm // 2).astype(np.int32)
+    st = torch.from_numpy(sel).to(d_idw.device)
+    gi, gd, gv = (t[st].cpu().numpy() for t in (d_idw, d_ok, v_ok))
+    t0 = time.perf_counter()
+    tree = oracle.Tree(w.x_cm, w.y_cm, w.z_m)
+    ri, rd, rv = run_oracle(w, qx, qy, tree)
+    tree.close()
+    out = compare_with_oracle(gi, gd, gv, ri, rd, rv)
+    out["nodes"] = int(sel.size)
+    out["sample"] = (f"{nodes} random nodes of the swath grid + 2 full rows in the gaps between "
+                     f"lines ({time.perf_counter() - t0:.1f} s of oracle on the host)")
+    return out
+
+
+def tile_configs(bg, torch, device, check):
+    """The two tile workloads (20,000 uniform soundings over 512 m, grid
+    256 x 256 at 2 m): IDW p=2 k=8 and kriging k=16 (spherical, nugget 0.25,
+    sill 100, range 50 m). Per tile: upload + hash build + gridding from
+    device-resident inputs, CUDA events, median of 30 after 5 warm-ups; and
+    the gridding alone on a built hash. Errors against the oracle on every
+    node."""
+    import oracle
+    dev = torch.device("cuda", device)
+    w = synth.tile(seed=1)
+    g = w.grid
+    ctx = bg.ctx_create(device)
+    grid = bg.grid_create(ctx, g.x0_cm, g.y0_cm, g.cell_cm, g.nx, g.ny)
+    x, y, z = (torch.from_numpy(a).to(dev) for a in (w.x_cm, w.y_cm, w.z_m))
+    d = torch.empty(g.m, device=dev)
+    v = torch.empty(g.m, device=dev)
+    vgm = bg.variogram(*VGM)
+    stream = torch.cuda.current_stream(dev)
+    runs = {"idw_p2_k8": lambda s: bg.interp_idw(s, grid, 8, 2.0, d),
+            "kriging_k16": lambda s: bg.interp_okrige(s, grid, 16, vgm, d, v)}
+    out = {"workload": "20,000 uniform soundings over a 512 m tile (seed 1), grid 256 x 256 "
+                       "at 2 m; device-resident inputs"}
+    qx, qy = oracle.grid_nodes(g.x0_cm, g.y0_cm, g.cell_cm, g.nx, g.ny)
+    tree = oracle.Tree(w.x_cm, w.y_cm, w.z_m) if check else None
+    for name, fn in runs.items():
+        full, interp = [], []
+        for it in range(35):
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e[0].record(stream)
+            s = bg.soundings_upload(ctx, x, y, z)
+            e[1].record(stream)
+            fn(s)
+            e[2].record(stream)
+            torch.cuda.synchronize()
+            bg.soundings_destroy(s)
+            if it >= 5:
+                full.append(e[0].elapsed_time(e[2]))
+                interp.append(e[1].elapsed_time(e[2]))
+        ms, ms_i = statistics.median(full), statistics.median(interp)
+        r = {"tile_latency_ms": ms, "nodes_per_s": g.m / (ms / 1e3),
+             "gridding_ms": ms_i, "gridding_nodes_per_s": g.m / (ms_i / 1e3),
+             "hash_build_ms": ms - ms_i}
+        if check:
+            if name.startswith("idw"):
+                ri = oracle.idw(w.x_cm, w.y_cm, w.z_m, qx, qy, 8, 2.0, tree=tree)
+                r["errors_vs_oracle"] = compare_with_oracle(d.cpu().numpy(), None, None, ri,
+                                                            None, None)
+            else:
+                rd, rv = oracle.okrige(w.x_cm, w.y_cm, w.z_m, qx, qy, 16, *VGM, tree=tree)
+                r["errors_vs_oracle"] = compare_with_oracle(None, d.cpu().numpy(),
+                                                            v.cpu().numpy(), None, rd, rv)
+        out[name] = r
+    if tree is not None:
+        tree.close()
+    bg.grid_destroy(grid)
+    bg.ctx_destroy(ctx)
+    return out
 
 
 def bench_ours(args):
@@ -567,11 +848,18 @@ def bench_ours(args):
     # the clock sampler starts before the warm-up, so that the start of
     # nvidia-smi falls outside the timed region; only the samples read while
     # the timed steps ran are kept
+    peaks = measure_alu_peaks(bg, local)
     with ClockSampler(local) as clk:
         for _ in range(args.warmup):
             step(False)
+        bg.profile_read(ctx)
+        bg.profile_enable(ctx, True)
+        clk.mark("sep_start")
         sep = [separate_step() for _ in range(2)]
         torch.cuda.synchronize()
+        clk.mark("sep_stop")
+        sep_prof = bg.profile_read(ctx)
+        bg.profile_enable(ctx, False)
         sep_ms = {"ms_per_step": statistics.mean(e[0].elapsed_time(e[3]) for e in sep),
                   "idw_k16_ms": statistics.mean(e[1].elapsed_time(e[2]) for e in sep),
                   "kriging_k32_ms": statistics.mean(e[2].elapsed_time(e[3]) for e in sep)}
@@ -621,7 +909,7 @@ def bench_ours(args):
     e2e_step()
     torch.cuda.synchronize()
     barrier()
-    e_steps = max(1, min(args.steps, 3))
+    e_steps = max(1, args.steps)
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record(stream)
@@ -639,14 +927,18 @@ def bench_ours(args):
         os.sched_setaffinity(0, saved_cpus)
     bad = int(torch.isnan(d_idw).sum() + torch.isnan(d_ok).sum())
 
+    # per-result error against the FP64 oracle at sampled nodes of the last step
+    errors = None
+    if rank == 0 and not args.no_oracle_check:
+        errors = oracle_check_swath(w, torch, d_idw, d_ok, v_ok, args.check_nodes)
+
     if rank == 0:
-        peaks = load_peaks()
-        # dominant kernel: the kriging solve, timed per launch by events on its stream
-        s_ms, s_launch, s_nodes = prof["kriging_solve"]
-        solve_avg_ms = s_ms / max(s_launch, 1)
-        nodes_per_launch = s_nodes / max(s_launch, 1)
-        achieved = okrige_flops_per_node() * nodes_per_launch / (solve_avg_ms / 1e3) / 1e12
+        mpeaks = load_peaks()
         clocks = clk.summary("start", "stop")
+        step_mhz = clocks.get("sm_mhz") or 2070.0
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        rl = rooflines(prof, sep_prof, peaks, mpeaks, step_mhz, sms, w, args.steps,
+                       clk.summary("sep_start", "sep_stop").get("sm_mhz") or step_mhz)
         out = {
             "metric": METRIC, "value": value, "unit": "nodes/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
@@ -661,34 +953,30 @@ def bench_ours(args):
             "step_ms": [round(t, 3) for t in per_step], "lead_ms": round(lead_ms, 3),
             "idw_nodes_per_s_alone": m / (sep_ms["idw_k16_ms"] / 1e3),
             "kriging_nodes_per_s_alone": m / (sep_ms["kriging_k32_ms"] / 1e3),
-            "roofline": {"bound": "alu",
-                         "kernel": "k_okrige_solve<32> (kriging k=32 solve, fused IDW k=16)",
-                         "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved / FP32_PEAK_TFLOPS,
-                         "traffic": SOLVE_DRAM_BYTES_PER_NODE * nodes_per_launch,
-                         "avg_launch_ms": solve_avg_ms, "nodes_per_launch": nodes_per_launch,
-                         "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
-                         "flops_per_node": okrige_flops_per_node(),
-                         "traffic_source": "ncu dram bytes of the same kernel on a 3.384M-node "
-                                           "swath, scaled per node",
-                         "hbm_peak_gbs_measured": peaks.get("hbm_gbs")},
+            "roofline": rl["kriging_solve"],
+            "rooflines": rl,
+            "alu_peaks_measured": peaks,
+            "errors_vs_oracle": errors,
             "e2e": {"value": ws * m / (e2e_ms / 1e3), "unit": "nodes/s",
                     "h2d_bytes_per_step": int(12 * w.x_cm.size),
-                    "d2h_bytes_per_step": int(12 * m), "ms_per_step": e2e_ms},
+                    "d2h_bytes_per_step": int(12 * m), "ms_per_step": e2e_ms, "steps": e_steps},
             "gpu_launches": int(launches), "clocks": clocks, "nan_outputs": bad,
         }
+        if not args.no_tiles:
+            out["tile_configs"] = tile_configs(bg, torch, local, not args.no_oracle_check)
         pool = None
         if not args.no_batched:
             pool = serving_pool(args.serving_pool)
-            out["batched"] = batched_measure(bg, torch, ctx, pool, args.batch_tiles, 3)
+            out["batched"] = batched_measure(bg, torch, ctx, pool, args.batch_tiles, 3,
+                                             0 if args.no_oracle_check else 256)
             out["batched"]["workload"] = (
                 "one launch sequence (graph of persistent kernels) over tiles of uneven size: "
                 "lognormal N (median 20k, 1k-200k), grid side 64-1024 at 1-4 m, IDW k=16 / "
                 "kriging k=32 50/50, drawn cyclically from the distinct tiles; device-resident")
         if not args.no_serving:
             pool = pool or serving_pool(args.serving_pool)
-            rates = [50, 200, 500, 1000, 2000] if args.serving else [500, 1000]
-            n_t = args.serving_tiles if args.serving else 300
+            rates = [50, 200, 500, 1000, 2000]
+            n_t = args.serving_tiles
             out["serving"] = {
                 "workload": (f"{len(pool)} distinct tiles drawn with replacement: lognormal N "
                              "(median 20k, 1k-200k), grid side 64-1024 at 1-4 m, IDW k=16 / "
@@ -725,10 +1013,9 @@ def main():
     ap.add_argument("--small", action="store_true", help="2-line swath (quick check / profiling)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--ref-nodes", type=int, default=256, help="reference arm: nodes per step")
-    ap.add_argument("--serving", action="store_true",
-                    help="full serving sweep: 50-2000 tiles/s, --serving-tiles tiles per rate")
-    ap.add_argument("--serving-tiles", type=int, default=2000)
+    ap.add_argument("--ref-nodes", type=int, default=50_000, help="reference arm: nodes per step")
+    ap.add_argument("--serving-tiles", type=int, default=1000,
+                    help="tiles per arrival rate of the serving sweep (50-2000 tiles/s)")
     ap.add_argument("--serving-pool", type=int, default=48)
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
@@ -737,6 +1024,11 @@ def main():
     ap.add_argument("--gridded-only", action="store_true",
                     help="only the gridded-input measurements (one JSON line of their own)")
     ap.add_argument("--batch-tiles", type=int, default=512)
+    ap.add_argument("--no-oracle-check", action="store_true",
+                    help="skip the per-result comparison with the FP64 oracle")
+    ap.add_argument("--check-nodes", type=int, default=100_000,
+                    help="random swath nodes compared with the oracle")
+    ap.add_argument("--no-tiles", action="store_true", help="skip the two tile workloads")
     args = ap.parse_args()
     if args.impl == "reference":
         bench_reference(args)

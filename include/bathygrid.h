@@ -391,6 +391,16 @@ bg_status bg_launch_count(uint64_t* out);
 bg_status bg_profile_enable(bg_ctx_t ctx, int on);
 bg_status bg_profile_read(bg_ctx_t ctx, double* ms, int64_t* launches, int64_t* units, int n);
 
+/* Measured ALU peak of a GPU, for rooflines of kernels that no memory or
+ * tensor-core bound describes. The paper has no counterpart: a measurement
+ * helper. kind: 0 FP32 FMA (flop/s, an FMA counts 2), 1 INT32 multiply-add
+ * (op/s), 2 INT32 add then xor (op/s, 2 per step), 3 FP64 FMA (flop/s). It
+ * runs about 0.5 s of kernels of independent dependency chains on every SM of
+ * `device` (CUDA events; best of three) and writes the rate to *ops_per_s
+ * and the SM clock measured inside the kernel (clock64 ticks per globaltimer
+ * ns) to *sm_mhz_out (may be NULL). Allocates a few KB of device memory. */
+bg_status bg_alu_peak(int device, int kind, double* ops_per_s, double* sm_mhz_out);
+
 #ifdef __cplusplus
 }
 #endif

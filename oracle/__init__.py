@@ -64,7 +64,7 @@ def _load():
     lib.oracle_solve.restype = ctypes.c_int
     lib.oracle_resample.argtypes = [P, i32, i32, i32, i32, i32, ctypes.c_int, P, P, i64, P, P]
     lib.oracle_resample.restype = ctypes.c_int
-    lib.oracle_tree_build.argtypes = [P, P, P, i64]
+    lib.oracle_tree_build.argtypes = [P, P, P, i64, ctypes.c_int]
     lib.oracle_tree_build.restype = P
     lib.oracle_tree_free.argtypes = [P]
     lib.oracle_tree_free.restype = None
@@ -94,13 +94,14 @@ class Tree:
     on large inputs. It keeps references to the arrays it was built from;
     pass the same x, y, z to the queries."""
 
-    def __init__(self, x, y, z):
+    def __init__(self, x, y, z, nthreads: int = 0):
         self.x = np.ascontiguousarray(x, dtype=np.int32)
         self.y = np.ascontiguousarray(y, dtype=np.int32)
         self.z = np.ascontiguousarray(z, dtype=np.float32)
         if not (self.x.shape == self.y.shape == self.z.shape):
             raise ValueError("shape mismatch")
-        self._h = _load().oracle_tree_build(_p(self.x), _p(self.y), _p(self.z), self.x.size)
+        self._h = _load().oracle_tree_build(_p(self.x), _p(self.y), _p(self.z), self.x.size,
+                                            nthreads)
         if not self._h:
             raise MemoryError("oracle_tree_build")
 

@@ -214,12 +214,13 @@ static void select_median(tree_pt* a, int64_t lo, int64_t hi, int64_t mid, int a
 typedef struct {
     oracle_tree* t;
     int64_t node, lo, hi;
-    int depth;
+    int depth, spawn_depth;
 } build_job;
 
 static void* build_node(void* p);
 
-static void build_range(oracle_tree* t, int64_t node, int64_t lo, int64_t hi, int depth) {
+static void build_range(oracle_tree* t, int64_t node, int64_t lo, int64_t hi, int depth,
+                        int spawn_depth) {
     int32_t x0 = INT32_MAX, y0 = INT32_MAX, x1 = INT32_MIN, y1 = INT32_MIN;
     for (int64_t j = lo; j < hi; ++j) {
         const tree_pt* q = &t->pt[j];
@@ -237,23 +238,23 @@ static void build_range(oracle_tree* t, int64_t node, int64_t lo, int64_t hi, in
     const int axis = ((int64_t)y1 - y0) > ((int64_t)x1 - x0) ? 1 : 0;
     const int64_t mid = lo + (hi - lo) / 2;
     select_median(t->pt, lo, hi, mid, axis);
-    /* the two halves are disjoint: build the lower one on a new thread near the root */
-    if (depth < 4) {
-        build_job job = {t, 2 * node + 1, lo, mid, depth + 1};
+    /* the two halves are disjoint: near the root, build the lower one on a new thread */
+    if (depth < spawn_depth) {
+        build_job job = {t, 2 * node + 1, lo, mid, depth + 1, spawn_depth};
         pthread_t th;
         if (pthread_create(&th, NULL, build_node, &job) == 0) {
-            build_range(t, 2 * node + 2, mid, hi, depth + 1);
+            build_range(t, 2 * node + 2, mid, hi, depth + 1, spawn_depth);
             pthread_join(th, NULL);
             return;
         }
     }
-    build_range(t, 2 * node + 1, lo, mid, depth + 1);
-    build_range(t, 2 * node + 2, mid, hi, depth + 1);
+    build_range(t, 2 * node + 1, lo, mid, depth + 1, spawn_depth);
+    build_range(t, 2 * node + 2, mid, hi, depth + 1, spawn_depth);
 }
 
 static void* build_node(void* p) {
     build_job* j = (build_job*)p;
-    build_range(j->t, j->node, j->lo, j->hi, j->depth);
+    build_range(j->t, j->node, j->lo, j->hi, j->depth, j->spawn_depth);
     return NULL;
 }
 
@@ -265,10 +266,12 @@ void oracle_tree_free(void* p) {
     free(t);
 }
 
-/* Build the tree over the valid soundings of (x, y, z). Returns NULL when
- * memory runs out. The tree keeps copies of the coordinates and upload
- * indices; queries still read depths from the caller's arrays. */
-void* oracle_tree_build(const int32_t* x, const int32_t* y, const float* z, int64_t n) {
+/* Build the tree over the valid soundings of (x, y, z) on up to nthreads
+ * threads (0: every online core). Returns NULL when memory runs out. The tree
+ * keeps copies of the coordinates and upload indices; queries still read
+ * depths from the caller's arrays. */
+void* oracle_tree_build(const int32_t* x, const int32_t* y, const float* z, int64_t n,
+                        int nthreads) {
     oracle_tree* t = (oracle_tree*)calloc(1, sizeof(oracle_tree));
     if (!t || n < 0) {
         free(t);
@@ -296,7 +299,9 @@ void* oracle_tree_build(const int32_t* x, const int32_t* y, const float* z, int6
             t->pt[j].id = (int32_t)p;
             ++j;
         }
-    if (nv > 0) build_range(t, 0, 0, nv, 0);
+    int spawn_depth = 0;
+    for (int th = default_threads(nthreads); th > 1; th >>= 1) ++spawn_depth;
+    if (nv > 0) build_range(t, 0, 0, nv, 0, spawn_depth);
     return t;
 }
 

@@ -25,7 +25,7 @@ OKRIGE = 1
 
 __all__ = [
     "BGError", "Variogram", "SoundingsInfo", "SPHERICAL", "EXPONENTIAL", "IDW", "OKRIGE",
-    "version", "launch_count", "profile_enable", "profile_read", "ctx_create", "ctx_destroy",
+    "version", "launch_count", "alu_peak", "ALU_KINDS", "profile_enable", "profile_read", "ctx_create", "ctx_destroy",
     "ctx_device_bytes", "grid_create", "grid_destroy",
     "soundings_upload", "soundings_info", "soundings_destroy", "interp_idw", "interp_okrige",
     "interp_idw_okrige", "interp_idw_okrige_host", "interp_idw_points", "interp_okrige_points", "BILINEAR", "CATMULL_ROM", "resample_points",
@@ -76,6 +76,19 @@ def launch_count() -> int:
     out = ctypes.c_uint64()
     check(_lib().bg_launch_count(ctypes.byref(out)), "bg_launch_count")
     return out.value
+
+
+ALU_KINDS = {"fp32_fma": 0, "int32_imad": 1, "int32_add_xor": 2, "fp64_fma": 3}
+
+
+def alu_peak(kind: str, device: int = 0):
+    """Measured ALU peak of `device` for one instruction kind (ALU_KINDS):
+    (ops/s, SM MHz the measuring kernel ran at). FMAs count 2 flops."""
+    ops = ctypes.c_double()
+    mhz = ctypes.c_double()
+    check(_lib().bg_alu_peak(device, ALU_KINDS[kind], ctypes.byref(ops), ctypes.byref(mhz)),
+          "bg_alu_peak")
+    return ops.value, mhz.value
 
 
 PROFILE_STAGES = ("hash_build", "idw", "kriging_knn_ids", "kriging_solve")

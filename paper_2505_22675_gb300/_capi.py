@@ -71,6 +71,8 @@ _SIGNATURES = {
     "bg_last_error": ([], ctypes.c_char_p),
     "bg_status_str": ([ctypes.c_int], ctypes.c_char_p),
     "bg_launch_count": ([ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
+    "bg_alu_peak": ([ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                     ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "bg_profile_enable": ([P, ctypes.c_int], ctypes.c_int),
     "bg_profile_read": ([P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
                          ctypes.POINTER(ctypes.c_int64), ctypes.c_int], ctypes.c_int),
