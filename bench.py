@@ -312,8 +312,10 @@ def serving_measure(bg, torch, ctx, pool, rate, n_tiles, seed):
     lat = [(r.t_done_us - r.t_submit_us) / 1e3 for r in res]
     span = (max(r.t_done_us for r in res) - min(r.t_submit_us for r in res)) / 1e6
     nodes = sum(r.nodes for r in res)
+    wait_q = [(r.t_start_us - r.t_submit_us) / 1e3 for r in res]
     serve = {"p50_ms": _percentile(lat, 50), "p99_ms": _percentile(lat, 99),
-             "nodes_per_s": nodes / span, "errors": sum(1 for r in res if r.status != 0)}
+             "nodes_per_s": nodes / span, "errors": sum(1 for r in res if r.status != 0),
+             "queue_p50_ms": _percentile(wait_q, 50), "queue_p99_ms": _percentile(wait_q, 99)}
 
     # plain path: one synchronous call sequence per tile, first come first served
     dev = torch.device("cuda", torch.cuda.current_device())

@@ -269,12 +269,16 @@ typedef struct bg_result {
     double t_done_us;          /* its grids were in depth_out / var_out */
 } bg_result;
 
-/* Queue a request; returns at once with a ticket. Requests are admitted in
- * arrival order when one of the context's stream slots is free and the
- * context's HBM budget (bg_ctx_create) covers the request's estimated device
- * memory; admitted requests run concurrently on the device (continuous
- * batching). A request whose estimate alone exceeds the budget is refused
- * with BG_ERR_OOM_BUDGET. Thread-safe. */
+/* Submit a request; returns with a ticket without waiting for any device
+ * work. Requests are admitted in arrival order when one of the context's
+ * stream slots is free and the context's HBM budget (bg_ctx_create) covers
+ * the request's estimated device memory; admitted requests run concurrently
+ * on the device (continuous batching). When nothing is queued ahead and a
+ * slot is free, the calling thread issues the request itself (host copy into
+ * pinned staging, asynchronous upload and kernel launches: tens of
+ * microseconds for a typical tile) before returning; otherwise the request is
+ * queued for the context's dispatcher thread. A request whose estimate alone
+ * exceeds the budget is refused with BG_ERR_OOM_BUDGET. Thread-safe. */
 bg_status bg_submit(bg_ctx_t ctx, const bg_request* req, uint64_t* ticket);
 
 /* Never blocks. BG_PENDING while the ticket runs; otherwise BG_OK with *out

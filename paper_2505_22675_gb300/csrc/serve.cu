@@ -1,14 +1,18 @@
 // Serving: continuous batching of gridding requests on one context.
 //
-// bg_submit queues a request and returns a ticket at once. A dispatcher
-// thread admits queued requests in arrival order whenever a stream slot is
-// free and the context's HBM budget covers the request's estimated device
-// memory; each admitted request runs on its slot's stream (host copy into
+// bg_submit returns a ticket for a request. When nothing is queued ahead of
+// it and a stream slot and the context's HBM budget are free, the calling
+// thread issues it at once; otherwise it is queued, and a dispatcher thread
+// admits queued requests in arrival order whenever a slot is free and the
+// budget covers the request's estimated device memory; each admitted request runs on its slot's stream (host copy into
 // pinned staging + bounding box on the host, async upload and hash build,
 // interpolation, async copy of the grids back), so requests that arrive while
-// others run overlap with them on the device. A host function queued behind
-// the work copies the grids into the caller's buffers and completes the
-// ticket; bg_poll never blocks, bg_wait blocks up to a timeout.
+// others run overlap with them on the device. An event recorded behind the
+// work marks the request's end; a completion thread polls the events of the
+// running slots, copies each finished request's grids into the caller's
+// buffers and completes its ticket (a polled event ends a request sooner than
+// a host function queued on the stream, which waits for a driver thread to
+// wake). bg_poll never blocks, bg_wait blocks up to a timeout.
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
@@ -45,7 +49,9 @@ struct Ticket {
 
 struct Slot {
     cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;  // recorded behind the request's last copy
     bool busy = false;
+    bool inflight = false;       // issued, end event not yet seen (server lock)
     char* pin_in = nullptr;      // pinned staging: x, y, z
     size_t pin_in_bytes = 0;
     float* pin_out = nullptr;    // pinned staging: depth (+ variance)
@@ -61,13 +67,18 @@ struct Server {
     std::mutex mu;
     std::condition_variable cv_work;   // dispatcher: new request or a slot freed
     std::condition_variable cv_done;   // waiters: a ticket completed
+    std::condition_variable cv_flight; // completion thread: a request was issued
     std::deque<Ticket*> queue;
     std::unordered_map<uint64_t, Ticket*> tickets;
     std::vector<Slot> slots;
     uint64_t next_id = 1;
     size_t reserved = 0;               // device bytes reserved by running requests
+    int inflight = 0;                  // slots issued and not yet completed
+    int issuing = 0;                   // slots admitted, still being issued
     bool stop = false;
+    bool stop_completer = false;
     std::thread worker;
+    std::thread completer;
     Clock::time_point t0;
     double now_us() const {
         return std::chrono::duration<double, std::micro>(Clock::now() - t0).count();
@@ -87,9 +98,10 @@ size_t request_bytes(const bg_request& r) {
     return b + 4096;
 }
 
-void CUDART_CB on_done(void* arg) {
-    // runs on a driver thread once the slot's stream reached this point
-    Slot* sl = static_cast<Slot*>(arg);
+// A slot's request has finished on the device (or failed): copy its grids
+// out of pinned staging into the caller's buffers, then free the slot and
+// complete the ticket. Completion thread, server lock not held.
+void complete_slot(Slot* sl) {
     Server* sv = sl->server;
     Ticket* t = sl->ticket;
     const int64_t m = t->nodes;
@@ -102,10 +114,40 @@ void CUDART_CB on_done(void* arg) {
     t->t_done = sv->now_us();
     t->done = true;
     sl->busy = false;
+    sl->inflight = false;
     sl->ticket = nullptr;
+    sv->inflight -= 1;
     sv->reserved -= t->reserve;
     sv->cv_done.notify_all();
     sv->cv_work.notify_all();
+}
+
+// Poll the end events of the issued slots while any is in flight; sleep on
+// cv_flight otherwise.
+void completer(Server* sv) {
+    cudaSetDevice(sv->ctx->device);
+    std::vector<Slot*> live;
+    std::unique_lock<std::mutex> lk(sv->mu);
+    for (;;) {
+        while (sv->inflight == 0 && (sv->issuing > 0 || !sv->stop_completer))
+            sv->cv_flight.wait(lk);
+        if (sv->inflight == 0) break;  // stopping, nothing left or being issued
+        live.clear();
+        for (auto& s : sv->slots)
+            if (s.inflight) live.push_back(&s);
+        lk.unlock();
+        bool any = false;
+        for (Slot* sl : live) {
+            const cudaError_t e = cudaEventQuery(sl->done);
+            if (e == cudaErrorNotReady) continue;
+            if (e != cudaSuccess && sl->ticket->status == BG_PENDING)
+                sl->ticket->status = cuda_fail(e, "request on the device");
+            complete_slot(sl);
+            any = true;
+        }
+        if (!any) std::this_thread::yield();
+        lk.lock();
+    }
 }
 
 bg_status grow_pinned(void** p, size_t* have, size_t need) {
@@ -120,6 +162,26 @@ bg_status grow_pinned(void** p, size_t* have, size_t need) {
     return BG_OK;
 }
 
+// Bounding box, valid count and out-of-range count of the valid soundings
+// (depth not NaN). Branch-free, so the compiler can vectorize it.
+__attribute__((optimize("O3"))) HostBBox host_bbox(const int32_t* x, const int32_t* y,
+                                                    const float* z, int64_t n) {
+    const int32_t lim = 1 << 30;
+    int32_t x0 = INT32_MAX, y0 = INT32_MAX, x1 = INT32_MIN, y1 = INT32_MIN;
+    int64_t nv = 0, oor = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        const int32_t xi = x[i], yi = y[i];
+        const bool v = z[i] == z[i];
+        x0 = std::min(x0, v ? xi : INT32_MAX);
+        y0 = std::min(y0, v ? yi : INT32_MAX);
+        x1 = std::max(x1, v ? xi : INT32_MIN);
+        y1 = std::max(y1, v ? yi : INT32_MIN);
+        nv += v;
+        oor += v & ((xi <= -lim) | (xi >= lim) | (yi <= -lim) | (yi >= lim));
+    }
+    return HostBBox{x0, y0, x1, y1, nv, (int32_t)oor};
+}
+
 // Issue one request on its slot (dispatcher thread, server lock not held).
 bg_status launch_request(Server* sv, Slot* sl, Ticket* t) {
     NvtxRange nvtx("serve request");
@@ -132,27 +194,16 @@ bg_status launch_request(Server* sv, Slot* sl, Ticket* t) {
     rc = grow_pinned((void**)&sl->pin_out, &sl->pin_out_bytes, (size_t)m * 8);
     if (rc != BG_OK) return rc;
 
-    // copy into pinned staging and take the bounding box on the way
+    // copy into pinned staging, then the bounding box of the valid soundings
     int32_t* px = (int32_t*)sl->pin_in;
     int32_t* py = px + n;
     float* pz = (float*)(py + n);
-    HostBBox bb{INT32_MAX, INT32_MAX, INT32_MIN, INT32_MIN, 0, 0};
-    const int32_t lim = 1 << 30;
-    for (int64_t i = 0; i < n; ++i) {
-        const int32_t xi = r.x_cm[i], yi = r.y_cm[i];
-        const float zi = r.z_m[i];
-        px[i] = xi;
-        py[i] = yi;
-        pz[i] = zi;
-        if (!std::isnan(zi)) {
-            bb.x0 = std::min(bb.x0, xi);
-            bb.y0 = std::min(bb.y0, yi);
-            bb.x1 = std::max(bb.x1, xi);
-            bb.y1 = std::max(bb.y1, yi);
-            ++bb.n_valid;
-            bb.out_of_range += (xi <= -lim || xi >= lim || yi <= -lim || yi >= lim);
-        }
+    if (n > 0) {
+        std::memcpy(px, r.x_cm, (size_t)n * 4);
+        std::memcpy(py, r.y_cm, (size_t)n * 4);
+        std::memcpy(pz, r.z_m, (size_t)n * 4);
     }
+    HostBBox bb = host_bbox(px, py, pz, n);
     t->snd = new (std::nothrow) bg_soundings_s();
     if (!t->snd) return BG_ERR_INTERNAL;
     t->snd->ctx = ctx;
@@ -176,60 +227,77 @@ bg_status launch_request(Server* sv, Slot* sl, Ticket* t) {
     return BG_OK;
 }
 
+// Launch an admitted request on its slot and hand the slot to the completion
+// thread (server lock not held; the slot is already marked busy).
+void issue(Server* sv, Slot* sl, Ticket* t) {
+    bg_status rc = launch_request(sv, sl, t);
+    cudaStream_t st = sl->stream;
+    if (rc != BG_OK) {
+        t->status = rc;  // the completion skips the copy-out
+        cudaStreamSynchronize(st);
+    }
+    // stream-ordered releases queued behind the copy-out
+    if (t->snd) {
+        free_soundings(t->snd, st);
+        delete t->snd;
+        t->snd = nullptr;
+    }
+    if (t->d_out) {
+        dfree(sv->ctx, t->d_out, t->d_out_bytes, st);
+        t->d_out = nullptr;
+    }
+    const cudaError_t e = cudaEventRecord(sl->done, st);
+    if (e != cudaSuccess) {
+        t->status = cuda_fail(e, "cudaEventRecord");
+        cudaStreamSynchronize(st);
+    }
+    {
+        // hand the slot to the completion thread (an event that could not
+        // be recorded is complete at once: the stream was synchronized)
+        std::lock_guard<std::mutex> g(sv->mu);
+        sl->inflight = true;
+        sv->inflight += 1;
+        sv->issuing -= 1;
+    }
+    sv->cv_flight.notify_one();
+}
+
+// A free slot for the request at the head of the queue, if one is free and
+// the budget admits it (server lock held); marks the slot busy.
+Slot* admit(Server* sv, Ticket* t) {
+    Slot* free_slot = nullptr;
+    for (auto& s : sv->slots)
+        if (!s.busy) {
+            free_slot = &s;
+            break;
+        }
+    if (!free_slot) return nullptr;
+    const size_t budget = sv->ctx->budget;
+    if (!(budget == 0 || sv->reserved == 0 || sv->reserved + t->reserve <= budget)) return nullptr;
+    free_slot->busy = true;
+    free_slot->ticket = t;
+    t->slot = free_slot;
+    sv->reserved += t->reserve;
+    sv->issuing += 1;
+    t->t_start = sv->now_us();
+    return free_slot;
+}
+
 void dispatcher(Server* sv) {
     cudaSetDevice(sv->ctx->device);
     std::unique_lock<std::mutex> lk(sv->mu);
     for (;;) {
         if (sv->stop && sv->queue.empty()) break;
-        Slot* free_slot = nullptr;
-        for (auto& s : sv->slots)
-            if (!s.busy) {
-                free_slot = &s;
-                break;
-            }
-        Ticket* t = nullptr;
-        if (free_slot && !sv->queue.empty()) {
-            Ticket* head = sv->queue.front();
-            const size_t budget = sv->ctx->budget;
-            const bool fits = budget == 0 || sv->reserved == 0 || sv->reserved + head->reserve <= budget;
-            if (fits) {
-                t = head;
-                sv->queue.pop_front();
-            }
-        }
-        if (!t) {
+        Ticket* t = sv->queue.empty() ? nullptr : sv->queue.front();
+        Slot* free_slot = t ? admit(sv, t) : nullptr;
+        if (!free_slot) {
             sv->cv_work.wait(lk);
             continue;
         }
-        free_slot->busy = true;
-        free_slot->ticket = t;
-        t->slot = free_slot;
-        sv->reserved += t->reserve;
-        t->t_start = sv->now_us();
+        sv->queue.pop_front();
         lk.unlock();
 
-        bg_status rc = launch_request(sv, free_slot, t);
-        cudaStream_t st = free_slot->stream;
-        if (rc != BG_OK) {
-            t->status = rc;  // on_done skips the copy-out
-            cudaStreamSynchronize(st);
-        }
-        // stream-ordered releases queued behind the copy-out
-        if (t->snd) {
-            free_soundings(t->snd, st);
-            delete t->snd;
-            t->snd = nullptr;
-        }
-        if (t->d_out) {
-            dfree(sv->ctx, t->d_out, t->d_out_bytes, st);
-            t->d_out = nullptr;
-        }
-        const cudaError_t e = cudaLaunchHostFunc(st, on_done, free_slot);
-        if (e != cudaSuccess) {
-            t->status = cuda_fail(e, "cudaLaunchHostFunc");
-            cudaStreamSynchronize(st);
-            on_done(free_slot);
-        }
+        issue(sv, free_slot, t);
         lk.lock();
     }
 }
@@ -246,10 +314,12 @@ Server* get_server(bg_ctx_s* ctx) {
     cudaSetDevice(ctx->device);
     for (auto& s : sv->slots) {
         cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking);
+        cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming);
         s.server = sv;
     }
     cudaSetDevice(prev);
     sv->worker = std::thread(dispatcher, sv);
+    sv->completer = std::thread(completer, sv);
     ctx->server = sv;
     return sv;
 }
@@ -298,6 +368,7 @@ bg_status bg_submit(bg_ctx_t ctx, const bg_request* req, uint64_t* ticket) {
     Server* sv = get_server(ctx);
     Ticket* t = new (std::nothrow) Ticket();
     if (!t) return BG_ERR_INTERNAL;
+    Slot* inline_slot = nullptr;
     t->req = r;
     t->nodes = (int64_t)r.nx * r.ny;
     t->reserve = request_bytes(r);
@@ -316,10 +387,21 @@ bg_status bg_submit(bg_ctx_t ctx, const bg_request* req, uint64_t* ticket) {
         t->id = sv->next_id++;
         t->t_submit = sv->now_us();
         sv->tickets[t->id] = t;
-        sv->queue.push_back(t);
+        // nothing queued ahead and a slot free: issue it on this thread (no
+        // hand-off to the dispatcher), else queue it in arrival order
+        if (sv->queue.empty()) inline_slot = admit(sv, t);
+        if (!inline_slot) sv->queue.push_back(t);
+        *ticket = t->id;
     }
-    sv->cv_work.notify_all();
-    *ticket = t->id;
+    if (inline_slot) {
+        int prev = 0;
+        cudaGetDevice(&prev);
+        if (prev != ctx->device) cudaSetDevice(ctx->device);
+        issue(sv, inline_slot, t);
+        if (prev != ctx->device) cudaSetDevice(prev);
+    } else {
+        sv->cv_work.notify_all();
+    }
     return BG_OK;
 }
 
@@ -432,11 +514,19 @@ bg_status bg_serve_shutdown(bg_ctx_t ctx) {
     }
     sv->cv_work.notify_all();
     if (sv->worker.joinable()) sv->worker.join();
+    {
+        // the completion thread drains what is still running, then ends
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->stop_completer = true;
+    }
+    sv->cv_flight.notify_all();
+    if (sv->completer.joinable()) sv->completer.join();
     for (auto& s : sv->slots) {
         if (s.stream) {
             cudaStreamSynchronize(s.stream);
             cudaStreamDestroy(s.stream);
         }
+        if (s.done) cudaEventDestroy(s.done);
         if (s.pin_in) cudaFreeHost(s.pin_in);
         if (s.pin_out) cudaFreeHost(s.pin_out);
     }
