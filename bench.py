@@ -366,6 +366,7 @@ def batched_measure(bg, torch, ctx, pool, n_tiles, steps, check_nodes_per_tile=2
     nodes = sum(t["grid_spec"][3] * t["grid_spec"][4] for t in tiles)
     b = bg.batch_create(ctx, tiles)
     best = bg.batch_tune(b)
+    tuned = bg.batch_config(b)
     for _ in range(2):
         bg.batch_run(b)
     torch.cuda.synchronize()
@@ -398,7 +399,8 @@ def batched_measure(bg, torch, ctx, pool, n_tiles, steps, check_nodes_per_tile=2
     return {"tiles": n_tiles, "distinct_tiles": len(pool), "nodes": int(nodes),
             "ms_per_batch": ms, "nodes_per_s": nodes / (ms / 1e3),
             "per_tile_calls_ms": per_tile_ms, "per_tile_calls_nodes_per_s": nodes / (per_tile_ms / 1e3),
-            "cell_target_tuned": best, "status_flags": status, "errors_vs_oracle": check}
+            "cell_target_tuned": best, "tuned": tuned, "status_flags": status,
+            "errors_vs_oracle": check}
 
 
 def oracle_check_batch(torch, tiles, pool, n_tiles, per_tile=256, seed=5):

@@ -340,8 +340,25 @@ bg_status bg_batch_run(bg_batch_t b, void* cuda_stream);
  * next run records a new graph. */
 bg_status bg_batch_set_cell_target(bg_batch_t b, float soundings_per_cell);
 
-/* Autotune the cell target: time a few targets on this batch (each run is a
- * real run, so outputs are written) and keep the fastest; *best_out gets it. */
+/* Launch shape of the next runs (the next run records a new graph):
+ *   knn_strip: grid nodes a k-NN thread takes one after another along x (1, 2
+ *     or 4; from the second on, the previous node's k-th distance plus the
+ *     step bounds the search), i.e. (16 knn_strip) x 8 nodes per k-NN item;
+ *   solve_item: block batches of kriging systems per claimed solve item (1, 2,
+ *     4, 8 or 16; 256 systems at K = 32 for 8, the default).
+ * Results never depend on the shape. Other values: BG_ERR_INVALID_ARG. */
+bg_status bg_batch_set_shape(bg_batch_t b, int knn_strip, int solve_item);
+
+/* The batch's current cell target, k-NN strip length and solve item size
+ * (any pointer may be NULL). */
+bg_status bg_batch_get_config(bg_batch_t b, float* soundings_per_cell, int* knn_strip,
+                              int* solve_item);
+
+/* Autotune the cell target, the k-NN strip length and the solve item size by
+ * coordinate descent: time each candidate of one knob on this batch with the
+ * others at their best so far (every run is a real run, so outputs are
+ * written) and keep the fastest. *best_out gets the cell target;
+ * bg_batch_get_config gives all three. Results never depend on the choice. */
 bg_status bg_batch_tune(bg_batch_t b, void* cuda_stream, float* best_out);
 
 /* After the last run has finished: bit 0 = a tile had a coordinate outside

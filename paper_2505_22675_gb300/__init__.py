@@ -31,7 +31,7 @@ __all__ = [
     "interp_idw_okrige", "interp_idw_okrige_host", "interp_idw_points", "interp_okrige_points", "BILINEAR", "CATMULL_ROM", "resample_points",
     "resample_grid",
     "variogram", "interp_idw_noalloc", "submit", "poll", "wait", "cancel", "serve_stats",
-    "serve_shutdown", "Request", "Result", "Batch", "batch_create", "batch_run", "batch_tune",
+    "serve_shutdown", "Request", "Result", "Batch", "batch_create", "batch_run", "batch_tune", "batch_set_shape", "batch_config",
     "batch_set_cell_target", "batch_status", "batch_destroy",
 ]
 
@@ -433,7 +433,24 @@ def batch_set_cell_target(b: Batch, soundings_per_cell: float) -> None:
           "bg_batch_set_cell_target")
 
 
+def batch_set_shape(b: Batch, knn_strip: int, solve_item: int) -> None:
+    """k-NN nodes per thread along x (1, 2, 4) and solve block batches per
+    claimed item (1, 2, 4, 8, 16) of the next runs; results do not change."""
+    check(_lib().bg_batch_set_shape(b.handle, int(knn_strip), int(solve_item)),
+          "bg_batch_set_shape")
+
+
+def batch_config(b: Batch) -> dict:
+    """{'soundings_per_cell', 'knn_strip', 'solve_item'} of the batch."""
+    ppc, strip, item = ctypes.c_float(), ctypes.c_int(), ctypes.c_int()
+    check(_lib().bg_batch_get_config(b.handle, ctypes.byref(ppc), ctypes.byref(strip),
+                                     ctypes.byref(item)), "bg_batch_get_config")
+    return {"soundings_per_cell": ppc.value, "knn_strip": strip.value, "solve_item": item.value}
+
+
 def batch_tune(b: Batch, stream=None) -> float:
+    """Tune the cell target, k-NN strip and solve item size (batch_config
+    gives all three); returns the cell target."""
     best = ctypes.c_float()
     check(_lib().bg_batch_tune(b.handle, _stream(stream, *(t["depth_out"] for t in b._keep[:1])),
                                ctypes.byref(best)), "bg_batch_tune")

@@ -114,6 +114,9 @@ _SIGNATURES = {
     "bg_batch_run": ([P, P], ctypes.c_int),
     "bg_batch_set_cell_target": ([P, ctypes.c_float], ctypes.c_int),
     "bg_batch_tune": ([P, P, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
+    "bg_batch_set_shape": ([P, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+    "bg_batch_get_config": ([P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int),
+                             ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "bg_batch_status": ([P, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "bg_batch_destroy": ([P], ctypes.c_int),
     "bg_interp_idw_noalloc": ([P, P, P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,

@@ -12,14 +12,20 @@
 //      exclusive scan, scatter (cell_start holds positions in the shared
 //      record array, so each tile's hash is a window of it);
 //   4. per-tile summed-area tables (one block per tile);
-//   5. a persistent kernel drains (tile, 16 x 8 node patch) items: IDW tiles
-//      are gridded in place, kriging tiles get their neighbour ids;
-//   6. a persistent kernel per kriging system size drains (tile, 64-system)
-//      items (okrige_solve_block);
+//   5. a persistent kernel drains (tile, 16 S x 8 node patch) items, a thread
+//      gridding S consecutive nodes along x (S = 1, 2 or 4: the strip
+//      length; from the second node on, the previous node's K-th distance
+//      plus the step bounds the search): IDW tiles are gridded in place,
+//      kriging tiles get their neighbour ids;
+//   6. a persistent kernel per kriging system size drains (tile, nb x 16
+//      warps' systems) items (okrige_solve_block), nb block batches per
+//      claimed item;
 //   7. a wide-key pass, which returns at once unless a node's bound needed
 //      more than the packed key's bits.
 // Items are claimed with a global atomic counter, so uneven tiles balance
-// across the SMs. Results are bitwise those of the per-grid calls.
+// across the SMs. Results are bitwise those of the per-grid calls, whatever
+// the cell target, strip length and solve item size (bg_batch_tune picks
+// those three by timing runs).
 #include <algorithm>
 #include <cmath>
 #include <new>
@@ -56,7 +62,8 @@ constexpr int kChunk = 4096;      // soundings per block in the per-sounding ker
 constexpr int kBT = 256;          // threads of those kernels
 constexpr int kItemThreads = 128;
 constexpr int kKnnThreads = 64;  // k-NN blocks: a 16 KB heap, 13 blocks (26 warps) per SM
-constexpr int kBatchSolveBlocks = 8;  // block batches per claimed item (256 systems at K = 32), one atomic
+constexpr int kBatchSolveBlocks = 8;  // default block batches per claimed item (256 systems at K = 32)
+constexpr int kStrips[3] = {1, 2, 4};  // k-NN strip lengths the batch offers
 // The persistent solve runs 8-warp blocks, 2 per SM (128 registers, dynamic
 // shared memory), like the per-grid kernels: two blocks in different phases
 // of the long unrolled solve wait far less for instruction fetch than 3 or 4
@@ -259,7 +266,10 @@ __device__ __forceinline__ HashView tile_view(const TileDesc& d, const int4* ori
     return h;
 }
 
-// 5. persistent k-NN items: IDW in place, kriging ids
+// 5. persistent k-NN items: IDW in place, kriging ids. An item is a
+// (16 kS) x 8 node patch of one tile; warp w covers its (8 kS) x 4 quarter,
+// each thread a strip of kS nodes along x.
+template <int kS>
 __global__ void __launch_bounds__(kKnnThreads) k_batch_knn(
     const TileDesc* __restrict__ td, int T, const int64_t* __restrict__ item_off, int64_t items,
     unsigned long long* __restrict__ ctr, const int4* __restrict__ orig,
@@ -283,37 +293,38 @@ __global__ void __launch_bounds__(kKnnThreads) k_batch_knn(
         const TileDesc& d = td[t];
         const HashView h = tile_view(d, orig, rec, cell_start, sat);
         const GridView g = d.g;
+        const int gx = (g.nx + 16 * kS - 1) / (16 * kS);
         const int64_t patch = item - __ldg(item_off + t);
-        // the 16 x 8 patch in two halves of 16 x 4 (two warps each)
-        for (int half = 0; half < 2; ++half) {
-            const NodeIdx nd = patch_node((int)(patch % d.gx), (int)(patch / d.gx), warp + 2 * half,
-                                          lane);
-            if (nd.i >= g.nx || nd.j >= g.ny) continue;
-            const int64_t node = (int64_t)nd.j * g.nx + nd.i;
-            const int qx = g.x0 + nd.i * g.cell + g.cell / 2;
-            const int qy = g.y0 + nd.j * g.cell + g.cell / 2;
-            const int k = d.k;
-            int keff = 0;
-            if (h.n_valid > 0) {
-                const Bound b = knn_bound_rt(h, qx, qy, d.method == 0 ? k : d.K);
-                if (!packed_fits(h, b.tau0)) {
-                    *wide = 1;
-                    continue;
-                }
-                keff = min(knn_scan_heap_rt<kKnnThreads>(h, qx, qy, b, hp,
-                                                         d.method == 0 ? k : d.K), k);
-            }
-            const int bits = h.idx_bits;
-            const uint64_t mask = (1ull << bits) - 1;
+        const int px = (int)(patch % gx), py = (int)(patch / gx);
+        const int k = d.k, kc = d.method == 0 ? k : d.K;
+        const int bits = h.idx_bits;
+        const uint64_t mask = (1ull << bits) - 1;
+        // the node's neighbours, sorted ascending in hp[0 .. cnt)
+        auto emit = [&](int i, int cnt, int j) {
+            const int64_t node = (int64_t)j * g.nx + i;
+            const int keff = min(cnt, k);
             if (d.method == 0) {
-                d.depth[node] = idw_from(h, keff, d.power, [&](int i, uint64_t& dd, int& ii) {
-                    const uint64_t key = hp[i * kKnnThreads];
+                d.depth[node] = idw_from(h, keff, d.power, [&](int q, uint64_t& dd, int& ii) {
+                    const uint64_t key = hp[q * kKnnThreads];
                     dd = key >> bits;
                     ii = (int)(key & mask);
                 });
             } else {
                 emit_ids<kKnnThreads>(d.ids + node * k, hp, k, keff, mask);
             }
+        };
+        // the (16 kS) x 8 patch in two halves of (16 kS) x 4 (two warps each)
+        for (int half = 0; half < 2; ++half) {
+            const int w = warp + 2 * half;
+            const int i0 = px * 16 * kS + (w & 1) * 8 * kS + (lane & 7) * kS;
+            const int j = py * 8 + (w >> 1) * 4 + (lane >> 3);
+            if (i0 >= g.nx || j >= g.ny) continue;
+            if (h.n_valid == 0) {
+                for (int i = i0; i < min(i0 + kS, g.nx); ++i) emit(i, 0, j);
+                continue;
+            }
+            auto emit_j = [&](int i, int cnt) { emit(i, cnt, j); };
+            knn_strip<kKnnThreads, decltype(emit_j), true, kS>(h, g, kc, i0, j, hp, wide, emit_j);
         }
     }
 }
@@ -326,7 +337,7 @@ __global__ void __launch_bounds__(kBatchSolveWarps * 32, kBatchSolveBlocksPerSM)
     const TileDesc* __restrict__ td, const int* __restrict__ tiles, int nt,
     const int64_t* __restrict__ off, int64_t items, unsigned long long* __restrict__ ctr,
     const int4* __restrict__ orig, const int4* __restrict__ rec, const int* __restrict__ cell_start,
-    const int* __restrict__ sat) {
+    const int* __restrict__ sat, int nb) {
     extern __shared__ __align__(16) float smem[];
     __shared__ long long s_item;
     __shared__ int s_j;
@@ -355,8 +366,8 @@ __global__ void __launch_bounds__(kBatchSolveWarps * 32, kBatchSolveBlocksPerSM)
         __syncthreads();
         const long long item = s_item;
         if (item >= items) break;
-        const int64_t b0 = (item - __ldg(off + s_j)) * kBatchSolveBlocks;
-        for (int b = 0; b < kBatchSolveBlocks; ++b)
+        const int64_t b0 = (item - __ldg(off + s_j)) * nb;
+        for (int b = 0; b < nb; ++b)
             okrige_solve_block<K, false, false, kBatchSolveWarps>(
                 s_h, s_g, s_k, s_p, 0, (int64_t)s_g.nx * s_g.ny, s_ids, s_depth, s_var, b0 + b, smem);
         __syncthreads();  // the next item overwrites the staged descriptor
@@ -420,15 +431,20 @@ struct bg_batch_s {
     bg_ctx_s* ctx = nullptr;
     int T = 0;
     float ppc = 2.0f;                      // soundings per hash cell (tuned)
+    int strip = 1;                         // k-NN nodes per thread along x (tuned)
+    int solve_nb = bg::kBatchSolveBlocks;  // solve block batches per claimed item (tuned)
+    int off_nb = 0;                        // solve_nb the groups' item offsets hold
     std::vector<bg::TileDesc> host_desc;
     int64_t total_n = 0, total_cells = 0, total_sat = 0, total_ids = 0;
-    int64_t knn_items = 0;
+    int64_t knn_items = 0;                 // 16 x 8 patches (wide pass)
+    int64_t knn_items_s[3] = {0, 0, 0};    // k-NN items per strip length 1, 2, 4
     struct Group {
         int K;
         int nt;
         int64_t items;
         int* tiles;       // device: tile indices
         int64_t* off;     // device: item prefix (nt + 1)
+        std::vector<int64_t> nodes;  // host: nodes of each tile of the group
     };
     std::vector<Group> groups;
     // device buffers (one allocation, carved)
@@ -436,7 +452,8 @@ struct bg_batch_s {
     size_t mem_bytes = 0;
     bg::TileDesc* d_desc = nullptr;
     int64_t* d_soff = nullptr;
-    int64_t* d_item_off = nullptr;
+    int64_t* d_item_off = nullptr;         // 16 x 8 patch prefix (wide pass)
+    int64_t* d_item_off_s[3] = {nullptr, nullptr, nullptr};  // k-NN item prefix per strip
     int4* d_orig = nullptr;
     int4* d_rec = nullptr;
     int* d_cell_start = nullptr;
@@ -480,9 +497,20 @@ void enqueue_batch(bg_batch_s* b, cudaStream_t st) {
     note_launches(6 + (n > 0 ? 3 : 0));
     // persistent kernels: as many blocks as an SM keeps resident drain the item lists
     if (b->knn_items > 0) {
-        k_batch_knn<<<(unsigned)std::min<int64_t>(b->knn_items, 152 * 13), kKnnThreads, 0, st>>>(
-            b->d_desc, T, b->d_item_off, b->knn_items, b->d_ctr, b->d_orig, b->d_rec,
-            b->d_cell_start, b->d_sat, b->d_flags);
+        const int si = b->strip == 4 ? 2 : b->strip == 2 ? 1 : 0;
+        const int64_t ki = b->knn_items_s[si];
+        const unsigned kg = (unsigned)std::min<int64_t>(ki, 152 * 13);
+#define BG_KNN(SS)                                                                               \
+    k_batch_knn<SS><<<kg, kKnnThreads, 0, st>>>(b->d_desc, T, b->d_item_off_s[si], ki, b->d_ctr, \
+                                                b->d_orig, b->d_rec, b->d_cell_start, b->d_sat,  \
+                                                b->d_flags)
+        if (b->strip == 4)
+            BG_KNN(4);
+        else if (b->strip == 2)
+            BG_KNN(2);
+        else
+            BG_KNN(1);
+#undef BG_KNN
         k_batch_wide<<<(unsigned)std::min<int64_t>(b->knn_items, 152 * 4), kItemThreads, 0, st>>>(
             b->d_desc, T, b->d_item_off, b->knn_items, b->d_orig, b->d_rec, b->d_cell_start,
             b->d_sat, b->d_flags);
@@ -496,7 +524,7 @@ void enqueue_batch(bg_batch_s* b, cudaStream_t st) {
 #define BG_SOLVE(KK)                                                                              \
     k_batch_solve<KK><<<grid, kBatchSolveWarps * 32, kBatchSolveWarps * Geo<KK>::WARP_FLOATS * 4, st>>>(b->d_desc, G.tiles, G.nt, G.off, G.items, \
                                                         ctr, b->d_orig, b->d_rec,                 \
-                                                        b->d_cell_start, b->d_sat)
+                                                        b->d_cell_start, b->d_sat, b->solve_nb)
         switch (G.K) {
             case 4: BG_SOLVE(4); break;
             case 8: BG_SOLVE(8); break;
@@ -517,6 +545,24 @@ cudaError_t set_batch_solve_smem() {
     BG_SMEM(4) BG_SMEM(8) BG_SMEM(16) BG_SMEM(32)
 #undef BG_SMEM
     return e;
+}
+
+// The solve groups' item prefixes for the current solve item size: a tile of m
+// nodes needs ceil(m / systems per item) items. Synchronous (never during
+// capture); no graph may be running that reads the old offsets.
+bg_status set_solve_offsets(bg_batch_s* b) {
+    if (b->off_nb == b->solve_nb) return BG_OK;
+    for (auto& G : b->groups) {
+        const int sys_per_item = kBatchSolveWarps * (32 / (G.K / kR)) * kRounds * b->solve_nb;
+        std::vector<int64_t> go(G.nodes.size() + 1, 0);
+        for (size_t j = 0; j < G.nodes.size(); ++j)
+            go[j + 1] = go[j] + (G.nodes[j] + sys_per_item - 1) / sys_per_item;
+        G.items = go.back();
+        const cudaError_t e = cudaMemcpy(G.off, go.data(), 8 * go.size(), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(e, "solve item offsets");
+    }
+    b->off_nb = b->solve_nb;
+    return BG_OK;
 }
 
 bg_status drop_graph(bg_batch_s* b) {
@@ -573,6 +619,7 @@ bg_status bg_batch_create(bg_ctx_t ctx, const bg_tile* tiles, int n_tiles, bg_ba
     b->T = n_tiles;
     b->host_desc.resize(n_tiles);
     std::vector<int64_t> soff(n_tiles + 1, 0), item_off(n_tiles + 1, 0);
+    std::vector<std::vector<int64_t>> item_off_s(3, std::vector<int64_t>(n_tiles + 1, 0));
     const int Ks[4] = {4, 8, 16, 32};
     std::vector<std::vector<int>> gt(4);
     for (int t = 0; t < n_tiles; ++t) {
@@ -608,6 +655,10 @@ bg_status bg_batch_create(bg_ctx_t ctx, const bg_tile* tiles, int n_tiles, bg_ba
         soff[t + 1] = b->total_n;
         const int64_t m = (int64_t)r.nx * r.ny;
         item_off[t + 1] = item_off[t] + (int64_t)d.gx * ((r.ny + 7) / 8);
+        for (int si = 0; si < 3; ++si)
+            item_off_s[si][t + 1] = item_off_s[si][t] + (int64_t)((r.nx + 16 * kStrips[si] - 1) /
+                                                                  (16 * kStrips[si])) *
+                                                        ((r.ny + 7) / 8);
         if (r.method == 1) {
             b->total_ids += m * r.k;
             for (int q = 0; q < 4; ++q)
@@ -615,6 +666,7 @@ bg_status bg_batch_create(bg_ctx_t ctx, const bg_tile* tiles, int n_tiles, bg_ba
         }
     }
     b->knn_items = item_off[n_tiles];
+    for (int si = 0; si < 3; ++si) b->knn_items_s[si] = item_off_s[si][n_tiles];
     // carve one allocation
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -625,6 +677,8 @@ bg_status bg_batch_create(bg_ctx_t ctx, const bg_tile* tiles, int n_tiles, bg_ba
     const size_t o_desc = take(sizeof(TileDesc) * std::max(1, n_tiles));
     const size_t o_soff = take(8 * (n_tiles + 1));
     const size_t o_item = take(8 * (n_tiles + 1));
+    size_t o_item_s[3];
+    for (int si = 0; si < 3; ++si) o_item_s[si] = take(8 * (n_tiles + 1));
     const size_t o_orig = take(16 * (size_t)b->total_n);
     const size_t o_rec = take(16 * (size_t)b->total_n);
     const size_t o_cs = take(4 * (size_t)(b->total_cells + 1));
@@ -661,6 +715,7 @@ bg_status bg_batch_create(bg_ctx_t ctx, const bg_tile* tiles, int n_tiles, bg_ba
     b->d_desc = (TileDesc*)(base + o_desc);
     b->d_soff = (int64_t*)(base + o_soff);
     b->d_item_off = (int64_t*)(base + o_item);
+    for (int si = 0; si < 3; ++si) b->d_item_off_s[si] = (int64_t*)(base + o_item_s[si]);
     b->d_orig = (int4*)(base + o_orig);
     b->d_rec = (int4*)(base + o_rec);
     b->d_cell_start = (int*)(base + o_cs);
@@ -682,23 +737,19 @@ bg_status bg_batch_create(bg_ctx_t ctx, const bg_tile* tiles, int n_tiles, bg_ba
     for (int q = 0; q < 4; ++q) {
         if (gt[q].empty()) continue;
         bg_batch_s::Group G{Ks[q], (int)gt[q].size(), 0, (int*)(base + o_gt[q]),
-                            (int64_t*)(base + o_go[q])};
-        const int sys_per_item = kBatchSolveWarps * (32 / (Ks[q] / kR)) * kRounds * kBatchSolveBlocks;
-        std::vector<int64_t> go(gt[q].size() + 1, 0);
-        for (size_t j = 0; j < gt[q].size(); ++j) {
-            const TileDesc& d = b->host_desc[gt[q][j]];
-            const int64_t m = (int64_t)d.g.nx * d.g.ny;
-            go[j + 1] = go[j] + (m + sys_per_item - 1) / sys_per_item;
-        }
-        G.items = go.back();
+                            (int64_t*)(base + o_go[q]), {}};
+        for (int t : gt[q])
+            G.nodes.push_back((int64_t)b->host_desc[t].g.nx * b->host_desc[t].g.ny);
         e = cudaMemcpyAsync(G.tiles, gt[q].data(), 4 * gt[q].size(), cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(G.off, go.data(), 8 * go.size(), cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) break;
-        b->groups.push_back(G);
+        b->groups.push_back(std::move(G));
         e = cudaStreamSynchronize(st);  // the host vectors go out of scope
         if (e != cudaSuccess) break;
     }
+    if (e == cudaSuccess && set_solve_offsets(b) != BG_OK) e = cudaErrorUnknown;
+    for (int si = 0; si < 3 && e == cudaSuccess; ++si)
+        e = cudaMemcpyAsync(b->d_item_off_s[si], item_off_s[si].data(), 8 * (n_tiles + 1),
+                            cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && n_tiles > 0)
         e = cudaMemcpyAsync(b->d_desc, b->host_desc.data(), sizeof(TileDesc) * n_tiles,
                             cudaMemcpyHostToDevice, st);
@@ -730,6 +781,13 @@ bg_status bg_batch_run(bg_batch_t b, void* cuda_stream) {
     const cudaStream_t user = (cudaStream_t)cuda_stream;
     cudaError_t e = cudaEventRecord(b->ev_in, user);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->ev_in, 0);
+    if (e == cudaSuccess && !b->exec) {
+        if (b->off_nb != b->solve_nb) {
+            // no replay of the previous graph may still read the offsets
+            e = cudaStreamSynchronize(b->stream);
+            if (e == cudaSuccess && set_solve_offsets(b) != BG_OK) e = cudaErrorUnknown;
+        }
+    }
     if (e == cudaSuccess && !b->exec) {
         const uint64_t before = g_launches.load();
         e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
@@ -763,39 +821,95 @@ bg_status bg_batch_set_cell_target(bg_batch_t b, float soundings_per_cell) {
     return BG_OK;
 }
 
+bg_status bg_batch_set_shape(bg_batch_t b, int knn_strip, int solve_item) {
+    if (!b || !(knn_strip == 1 || knn_strip == 2 || knn_strip == 4) ||
+        !(solve_item == 1 || solve_item == 2 || solve_item == 4 || solve_item == 8 ||
+          solve_item == 16)) {
+        set_error("knn_strip must be 1, 2 or 4 and solve_item 1, 2, 4, 8 or 16");
+        return BG_ERR_INVALID_ARG;
+    }
+    if (knn_strip != b->strip || solve_item != b->solve_nb) {
+        b->strip = knn_strip;
+        b->solve_nb = solve_item;
+        drop_graph(b);  // the next run captures a graph with the new shape
+    }
+    return BG_OK;
+}
+
+bg_status bg_batch_get_config(bg_batch_t b, float* soundings_per_cell, int* knn_strip,
+                              int* solve_item) {
+    if (!b) {
+        set_error("batch is NULL");
+        return BG_ERR_INVALID_ARG;
+    }
+    if (soundings_per_cell) *soundings_per_cell = b->ppc;
+    if (knn_strip) *knn_strip = b->strip;
+    if (solve_item) *solve_item = b->solve_nb;
+    return BG_OK;
+}
+
 bg_status bg_batch_tune(bg_batch_t b, void* cuda_stream, float* best_out) {
     if (!b) {
         set_error("batch is NULL");
         return BG_ERR_INVALID_ARG;
     }
-    const float cand[4] = {1.0f, 2.0f, 3.0f, 5.0f};
-    float best = b->ppc, best_ms = 1e30f;
     const cudaStream_t user = (cudaStream_t)cuda_stream;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     bg_status rc = BG_OK;
-    for (float c : cand) {
-        bg_batch_set_cell_target(b, c);
-        if ((rc = bg_batch_run(b, user)) != BG_OK) break;  // capture + warm-up
+    // one configuration: capture + warm-up run, then two timed replays
+    auto time_cfg = [&](float* ms) {
+        if ((rc = bg_batch_run(b, user)) != BG_OK) return false;
         cudaEventRecord(e0, user);
         for (int i = 0; i < 2 && rc == BG_OK; ++i) rc = bg_batch_run(b, user);
         cudaEventRecord(e1, user);
+        if (rc != BG_OK) return false;
         if (cudaEventSynchronize(e1) != cudaSuccess) {
             rc = cuda_fail(cudaGetLastError(), "tune");
-            break;
+            return false;
         }
-        float ms = 0;
-        cudaEventElapsedTime(&ms, e0, e1);
+        cudaEventElapsedTime(ms, e0, e1);
+        return true;
+    };
+    // coordinate descent: the cell target, then the k-NN strip length, then
+    // the solve item size, each with the others at their best so far
+    const float cells[4] = {1.0f, 2.0f, 3.0f, 5.0f};
+    const int strips[3] = {1, 2, 4}, items[4] = {2, 4, 8, 16};
+    float best_ppc = b->ppc, best_ms = 1e30f, ms = 0.0f;
+    int best_strip = b->strip, best_nb = b->solve_nb;
+    for (float c : cells) {
+        bg_batch_set_cell_target(b, c);
+        if (!time_cfg(&ms)) break;
         if (ms < best_ms) {
             best_ms = ms;
-            best = c;
+            best_ppc = c;
+        }
+    }
+    bg_batch_set_cell_target(b, best_ppc);
+    for (int sv : strips) {
+        if (rc != BG_OK) break;
+        bg_batch_set_shape(b, sv, best_nb);
+        if (!time_cfg(&ms)) break;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best_strip = sv;
+        }
+    }
+    for (int nb : items) {
+        if (rc != BG_OK) break;
+        bg_batch_set_shape(b, best_strip, nb);
+        if (!time_cfg(&ms)) break;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best_nb = nb;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    bg_batch_set_cell_target(b, best);
-    if (best_out) *best_out = best;
+    bg_batch_set_cell_target(b, best_ppc);
+    bg_batch_set_shape(b, best_strip, best_nb);
+    if (best_out) *best_out = best_ppc;
     return rc;
 }
 

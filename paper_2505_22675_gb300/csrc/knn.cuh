@@ -439,17 +439,18 @@ __device__ __forceinline__ NodeIdx strip_origin(int px, int py, int warp, int la
                    py * 8 + (warp >> 1) * 4 + (lane >> 3)};
 }
 
-// Packed-key k-NN of nodes (i0 .. i0 + kStrip - 1, j) with the kc best in the
+// Packed-key k-NN of nodes (i0 .. i0 + kLen - 1, j) with the kc best in the
 // shared-memory heap hp (stride S). emit(i, cnt) runs after each node with its
-// keys sorted ascending in hp[0 .. cnt); a node whose table bound does not
-// fit the packed key is left to the wide pass (*flag = 1).
-template <int S, class Emit, bool kSort = true>
+// keys sorted ascending in hp[0 .. cnt) (with kSort; else hp holds the max-heap);
+// a node whose table bound does not fit the packed key is left to the wide
+// pass (*flag = 1).
+template <int S, class Emit, bool kSort = true, int kLen = kStrip>
 __device__ __forceinline__ void knn_strip(const HashView& h, const GridView& g, int kc, int i0,
                                           int j, uint64_t* hp, int* flag, Emit emit) {
     const int qy = g.y0 + j * g.cell + g.cell / 2;
     int64_t prev = -1;  // K-th squared distance of the previous node, -1 if none
     int cy = 0;
-    for (int s = 0; s < kStrip; ++s) {
+    for (int s = 0; s < kLen; ++s) {
         const int i = i0 + s;
         if (i >= g.nx) break;
         const int qx = g.x0 + i * g.cell + g.cell / 2;

@@ -14,8 +14,9 @@ Two ways to split the work, both without any exchange inside the path:
 
 `compute` is the per-rank gridding function; by default it is the CUDA
 library on the rank's device. The collective calls use torch.distributed on
-whatever backend the process group was created with (NCCL on GPUs, gloo on
-CPU for tests).
+whatever backend the process group was created with: their buffers live on
+the rank's current CUDA device when the group's backend is NCCL (which takes
+device tensors only), on the host for gloo.
 """
 from __future__ import annotations
 
@@ -85,31 +86,53 @@ def _collective(fn, *args, **kwargs):
         raise RankFailure(f"collective {getattr(fn, '__name__', fn)} failed: {e}") from e
 
 
+def _comm_device(dist, group):
+    """Where the collectives' buffers live: the current CUDA device for an
+    NCCL group, the host otherwise."""
+    import torch
+    if str(dist.get_backend(group)).lower() == "nccl":
+        return torch.device("cuda", torch.cuda.current_device())
+    return torch.device("cpu")
+
+
 def _broadcast_array(dist, arr, src, group, dtype):
     import torch
-    n = torch.tensor([0 if arr is None else arr.size], dtype=torch.int64)
+    dev = _comm_device(dist, group)
+    n = torch.tensor([0 if arr is None else arr.size], dtype=torch.int64, device=dev)
     _collective(dist.broadcast, n, src, group=group)
-    t = torch.from_numpy(np.ascontiguousarray(arr)) if arr is not None and dist.get_rank(group) == src \
-        else torch.empty(int(n.item()), dtype=dtype)
+    if arr is not None and dist.get_rank(group) == src:
+        t = torch.from_numpy(np.ascontiguousarray(arr)).to(dev)
+    else:
+        t = torch.empty(int(n.item()), dtype=dtype, device=dev)
     _collective(dist.broadcast, t, src, group=group)
-    return t.numpy()
+    return t.cpu().numpy()
+
+
+def _all_sizes(dist, size: int, group):
+    """Every rank's `size`, in rank order."""
+    import torch
+    dev = _comm_device(dist, group)
+    world = dist.get_world_size(group)
+    n = torch.tensor([size], dtype=torch.int64, device=dev)
+    sizes = [torch.zeros(1, dtype=torch.int64, device=dev) for _ in range(world)]
+    _collective(dist.all_gather, sizes, n, group=group)
+    return [int(s.item()) for s in sizes]
 
 
 def _gather_to_root(dist, piece: np.ndarray, group, root=0):
     """Concatenate equal-dtype 1-D pieces of varying lengths on `root`."""
     import torch
+    dev = _comm_device(dist, group)
     world = dist.get_world_size(group)
-    n = torch.tensor([piece.size], dtype=torch.int64)
-    sizes = [torch.zeros(1, dtype=torch.int64) for _ in range(world)]
-    _collective(dist.all_gather, sizes, n, group=group)
-    m = max(int(s.item()) for s in sizes)
-    buf = torch.zeros(m, dtype=torch.from_numpy(piece[:0]).dtype)
-    buf[:piece.size] = torch.from_numpy(piece)
+    sizes = _all_sizes(dist, piece.size, group)
+    m = max(sizes)
+    buf = torch.zeros(m, dtype=torch.from_numpy(piece[:0]).dtype, device=dev)
+    buf[:piece.size] = torch.from_numpy(piece).to(dev)
     parts = [torch.zeros_like(buf) for _ in range(world)]
     _collective(dist.all_gather, parts, buf, group=group)
     if dist.get_rank(group) != root:
         return None
-    return np.concatenate([p[:int(s.item())].numpy() for p, s in zip(parts, sizes)])
+    return np.concatenate([p[:s].cpu().numpy() for p, s in zip(parts, sizes)])
 
 
 # ------------------------------------------------------------------- default
@@ -197,9 +220,6 @@ def grid_tiles(tiles, group=None, compute: Callable | None = None, root: int = 0
     flat = np.concatenate(pieces) if pieces else np.zeros(0, np.float32)
     allflat = _gather_to_root(dist, flat, group, root)
     # every rank knows every owner, so rank-major order is reproducible on root
-    sizes = torch.tensor([flat.size], dtype=torch.int64)
-    per_rank = [torch.zeros(1, dtype=torch.int64) for _ in range(world)]
-    _collective(dist.all_gather, per_rank, sizes, group=group)
     if rank != root:
         return None
     out = [None] * len(tiles)

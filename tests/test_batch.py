@@ -87,8 +87,30 @@ def test_batch_equals_per_grid_calls_and_replays():
         torch.cuda.synchronize()
         for t, (rd, rv) in zip(tiles, ref):
             assert _same(t["depth_out"].cpu().numpy(), rd)
+        # every launch shape (k-NN strip, solve item size) gives the same grids
+        for strip in (1, 2, 4):
+            for item in (1, 4, 16):
+                bg.batch_set_shape(b, strip, item)
+                for t in tiles:
+                    t["depth_out"].fill_(-1.0)
+                    if t["var_out"] is not None:
+                        t["var_out"].fill_(-1.0)
+                bg.batch_run(b)
+                torch.cuda.synchronize()
+                for t, (rd, rv) in zip(tiles, ref):
+                    assert _same(t["depth_out"].cpu().numpy(), rd), (strip, item)
+                    if t["method"] == 1:
+                        assert _same(t["var_out"].cpu().numpy(), rv), (strip, item)
+        with pytest.raises(bg.BGError):
+            bg.batch_set_shape(b, 3, 8)
         best = bg.batch_tune(b)
-        assert best in (1.0, 2.0, 3.0, 5.0)
+        cfg = bg.batch_config(b)
+        assert best in (1.0, 2.0, 3.0, 5.0) and cfg["soundings_per_cell"] == best
+        assert cfg["knn_strip"] in (1, 2, 4) and cfg["solve_item"] in (2, 4, 8, 16)
+        bg.batch_run(b)
+        torch.cuda.synchronize()
+        for t, (rd, rv) in zip(tiles, ref):
+            assert _same(t["depth_out"].cpu().numpy(), rd)
         bg.batch_destroy(b)
     finally:
         bg.ctx_destroy(ctx)

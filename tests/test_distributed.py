@@ -125,6 +125,64 @@ def test_slabs_on_one_gpu_equal_the_unsplit_grid():
                 assert np.array_equal(v.view(np.uint32), full_v.view(np.uint32))
 
 
+def _nccl_rank_main(rank, world, port, out_dir):
+    import torch
+    import torch.distributed as dist
+    os.environ["NCCL_NVLS_ENABLE"] = "0"
+    torch.cuda.set_device(rank)
+    dist.init_process_group("nccl", init_method=f"tcp://127.0.0.1:{port}", rank=rank,
+                            world_size=world)
+    try:
+        w = synth.swath(seed=2, lines=2, pings=300, beams=256)
+        g = w.grid
+        spec = (g.x0_cm, g.y0_cm, g.cell_cm, g.nx, g.ny)
+        d, _ = D.grid_swath(w.x_cm, w.y_cm, w.z_m, spec, D.IDW, 16)
+        dk, vk = D.grid_swath(w.x_cm, w.y_cm, w.z_m, spec, D.OKRIGE, 32)
+        tiles = []
+        for tw, m in synth.batched_tiles(seed=4, count=5, scale=0.02):
+            tg = tw.grid
+            tiles.append(dict(x_cm=tw.x_cm, y_cm=tw.y_cm, z_m=tw.z_m, method=m, k=16 if m == 0 else 32,
+                              grid_spec=(tg.x0_cm, tg.y0_cm, tg.cell_cm, tg.nx, tg.ny)))
+        res = D.grid_tiles(tiles)
+        if rank == 0:
+            np.save(os.path.join(out_dir, "idw.npy"), d)
+            np.save(os.path.join(out_dir, "okd.npy"), dk)
+            np.save(os.path.join(out_dir, "okv.npy"), vk)
+            for i, (td, tv) in enumerate(res):
+                np.save(os.path.join(out_dir, f"tile{i}_d.npy"), td)
+                if tv is not None:
+                    np.save(os.path.join(out_dir, f"tile{i}_v.npy"), tv)
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.gpu
+def test_nccl_group_runs_the_partitioned_paths(tmp_path):
+    """grid_swath and grid_tiles on an NCCL process group (one rank on this
+    GPU: the collectives' buffers must be device tensors) give bitwise the
+    single-GPU grids."""
+    import torch.multiprocessing as mp
+    mp.spawn(_nccl_rank_main, args=(1, _free_port(), str(tmp_path)), nprocs=1, join=True)
+    w = synth.swath(seed=2, lines=2, pings=300, beams=256)
+    g = w.grid
+    spec = (g.x0_cm, g.y0_cm, g.cell_cm, g.nx, g.ny)
+    run = D.library_compute(0)
+    vgm = (0, 0.25, 100.0, 50.0)
+    same = lambda a, b: np.array_equal(np.asarray(a, np.float32).view(np.uint32),
+                                       np.asarray(b, np.float32).view(np.uint32))
+    d, _ = run(w.x_cm, w.y_cm, w.z_m, spec, D.IDW, 16, 2.0, vgm)
+    assert same(np.load(tmp_path / "idw.npy"), d)
+    dk, vk = run(w.x_cm, w.y_cm, w.z_m, spec, D.OKRIGE, 32, 2.0, vgm)
+    assert same(np.load(tmp_path / "okd.npy"), dk) and same(np.load(tmp_path / "okv.npy"), vk)
+    for i, (tw, m) in enumerate(synth.batched_tiles(seed=4, count=5, scale=0.02)):
+        tg = tw.grid
+        rd, rv = run(tw.x_cm, tw.y_cm, tw.z_m, (tg.x0_cm, tg.y0_cm, tg.cell_cm, tg.nx, tg.ny), m,
+                     16 if m == 0 else 32, 2.0, vgm)
+        assert same(np.load(tmp_path / f"tile{i}_d.npy"), rd)
+        if m == D.OKRIGE:
+            assert same(np.load(tmp_path / f"tile{i}_v.npy"), rv)
+
+
 def _rank_leaves(rank, world, port, out_dir):
     import datetime
 
