@@ -60,9 +60,10 @@ struct Geo {
     static constexpr int TRI = K * (K + 1) / 2;           // packed lower triangle of A
     static constexpr int TRIP = (TRI + 3) / 4 * 4;        // the triangle padded to 16 bytes
     // per system: the fixed-point A as a packed lower triangle (row r at
-    // r (r + 1) / 2), one 16-byte record per row, and two column buffers for
-    // the Cholesky broadcasts (16-byte aligned); the stride is = G (mod 32) so
-    // that the G-thread groups of a warp spread over the banks
+    // r (r + 1) / 2), the rows' records (three arrays of K floats: x, y,
+    // Gamma_r0, in a region of 4 K), and two column buffers for the Cholesky
+    // broadcasts (16-byte aligned); the stride is = G (mod 32) so that the
+    // G-thread groups of a warp spread over the banks
     static constexpr int CB = TRIP + 4 * K;
     static constexpr int RAW = CB + 2 * K;
     static constexpr int SYS_FLOATS = RAW + ((G - RAW % 32) + 32) % 32;
@@ -137,6 +138,58 @@ __device__ __forceinline__ float gamma_pair_scaled(const ScaledVgm& v, float dx,
     }
 }
 
+// Packed two-lane FP32 arithmetic (one instruction for two IEEE single
+// operations, each lane rounded as its scalar counterpart): two floats in one
+// 64-bit register pair.
+__device__ __forceinline__ unsigned long long pk2(float a, float b) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void upk2(unsigned long long p, float& a, float& b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(p));
+}
+__device__ __forceinline__ unsigned long long add2(unsigned long long a, unsigned long long b) {
+    unsigned long long r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ unsigned long long sub2(unsigned long long a, unsigned long long b) {
+    unsigned long long r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ unsigned long long mul2(unsigned long long a, unsigned long long b) {
+    unsigned long long r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b,
+                                                   unsigned long long c) {
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
+// Two assembly entries of one column (x0, y0, gcc) from rows a and b at once,
+// in the fixed-point scale, spherical model: each lane takes exactly the
+// operations of (z + gcc) - gamma_pair_scaled<true>(sv, x - x0, y - y0).
+__device__ __forceinline__ void gamma_rows2_sph(const ScaledVgm& v, float xa, float xb, float ya,
+                                                float yb, float za, float zb, float x0, float y0,
+                                                float gcc, float& oa, float& ob) {
+    const unsigned long long dx = sub2(pk2(xa, xb), pk2(x0, x0));
+    const unsigned long long dy = sub2(pk2(ya, yb), pk2(y0, y0));
+    const unsigned long long t2 = mul2(fma2(dx, dx, mul2(dy, dy)), pk2(v.kinv2, v.kinv2));
+    float ta, tb;
+    upk2(t2, ta, tb);
+    ta = fminf(sqrt_approx(ta), 1.0f);  // the polynomial is the sill at t = 1
+    tb = fminf(sqrt_approx(tb), 1.0f);
+    const unsigned long long t = pk2(ta, tb);
+    const unsigned long long gm = fma2(t, fma2(pk2(v.k2, v.k2), mul2(t, t), pk2(v.k3, v.k3)),
+                                       pk2(v.c0s, v.c0s));
+    upk2(sub2(add2(pk2(za, zb), pk2(gcc, gcc)), gm), oa, ob);
+}
+
 // ------------------------------------------------------------ k-NN -> ids
 
 template <int K, bool kWide>
@@ -195,12 +248,28 @@ __device__ __forceinline__ void knn_ids_point_wide(const HashView& h, int qx, in
 
 __host__ __device__ constexpr int tri(int r) { return r * (r + 1) / 2; }
 
+// d0 += a * b0, d1 += a * b1 in one packed two-lane FMA (each lane a correctly
+// rounded fused multiply-add, so the results equal two fmaf calls)
+__device__ __forceinline__ void ffma2(float& d0, float& d1, float a, float b0, float b1) {
+    asm("{\n\t.reg .b64 d, a, b;\n\t"
+        "mov.b64 d, {%0, %1};\n\t"
+        "mov.b64 a, {%2, %2};\n\t"
+        "mov.b64 b, {%3, %4};\n\t"
+        "fma.rn.f32x2 d, a, b, d;\n\t"
+        "mov.b64 {%0, %1}, d;\n\t}"
+        : "+f"(d0), "+f"(d1)
+        : "f"(a), "f"(b0), "f"(b1));
+}
+
 // Cholesky column j of the register-held lower triangle: scale by the pivot
 // (one shuffle), then update the trailing rows with column j. Each thread
 // publishes its four entries of the column with one 16-byte store to a
 // column buffer and reads the group's entries back four rows per 16-byte
 // load (broadcast): fewer instructions than one shuffle per row. Two buffers
 // alternate by column, so one __syncwarp per column orders writes and reads.
+// A thread's columns c and c + G of one row take the same multiplier, and
+// the loaded rows c and c + G sit side by side in the 16-byte load: those two
+// updates go in one packed two-lane FMA (ffma2).
 // Expanded over j with an integer_sequence so every register index is a
 // compile-time constant (a nested #pragma unroll over the whole triangle is
 // beyond the unroller and would leave L in local memory).
@@ -239,13 +308,20 @@ __device__ __forceinline__ void chol_column(float (&L)[Geo<K>::LEN], float (&din
             const float4 q4 = *reinterpret_cast<const float4*>(col + 4 * tc);
             const float q[4] = {q4.x, q4.y, q4.z, q4.w};
 #pragma unroll
-            for (int sc = 0; sc < kR; ++sc) {
-                const int c = G * sc + tc;
-                if (c <= J) continue;
+            for (int s = 0; s < kR; ++s) {
+                if (G * (s + 1) - 1 <= J) continue;  // slot s holds no column beyond J
+                const float a = -L[Gm::off(s) + J];
 #pragma unroll
-                for (int s = 0; s < kR; ++s)
-                    if (G * (s + 1) - 1 >= c)
-                        L[Gm::off(s) + c] = fmaf(-L[Gm::off(s) + J], q[sc], L[Gm::off(s) + c]);
+                for (int p = 0; p < kR / 2; ++p) {
+                    const int c1 = G * (2 * p) + tc, c2 = c1 + G;
+                    const bool in1 = 2 * p <= s && c1 > J, in2 = 2 * p + 1 <= s && c2 > J;
+                    if (in1 && in2) {
+                        ffma2(L[Gm::off(s) + c1], L[Gm::off(s) + c2], a, q[2 * p], q[2 * p + 1]);
+                    } else {
+                        if (in1) L[Gm::off(s) + c1] = fmaf(a, q[2 * p], L[Gm::off(s) + c1]);
+                        if (in2) L[Gm::off(s) + c2] = fmaf(a, q[2 * p + 1], L[Gm::off(s) + c2]);
+                    }
+                }
             }
         }
     } else {
@@ -368,16 +444,13 @@ __device__ __forceinline__ void okrige_solve_block(const HashView& h, const Grid
     const int grp = lane / G, t = lane % G, gbase = grp * G;
     float* sysmem = smem + warp * Gm::WARP_FLOATS + grp * Gm::SYS_FLOATS;
     int* Aq = reinterpret_cast<int*>(sysmem);      // packed lower triangle: fixed-point A
-    // one 16-byte record per row r (neighbour r + 1): x and y minus those of
-    // neighbour 0 (cm), Gamma(neighbour r + 1, neighbour 0) in the fixed-point
-    // scale; after assembly the first two hold the row's output terms
+    // per row r (neighbour r + 1), three arrays of K: x and y minus those of
+    // neighbour 0 (cm) at T[r] and T[K + r], Gamma(neighbour r + 1,
+    // neighbour 0) in the fixed-point scale at T[2K + r]; four consecutive
+    // rows load as one 16-byte vector. After assembly T[r] and T[K + r] hold
+    // the row's output terms.
     float* T = sysmem + Gm::TRIP;
-    auto rec = [&](int r) {
-        if constexpr (G >= 4)
-            return *reinterpret_cast<const float4*>(T + 4 * r);
-        else
-            return make_float4(T[4 * r], T[4 * r + 1], T[4 * r + 2], 0.0f);
-    };
+    auto rec = [&](int r) { return make_float4(T[r], T[K + r], T[2 * K + r], 0.0f); };
     const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << gbase);
 
     for (int round = 0; round < kRounds; ++round) {
@@ -440,8 +513,8 @@ __device__ __forceinline__ void okrige_solve_block(const HashView& h, const Grid
                 }
             }
             const float ox = (float)(rr.x - r0.x), oy = (float)(rr.y - r0.y);
-            T[4 * r] = ox;
-            T[4 * r + 1] = oy;
+            T[r] = ox;
+            T[K + r] = oy;
             zr[s] = __int_as_float(rr.z);
             gr0[s] = real ? gamma_pair_f(p, ox, oy) : 0.0f;
             g0r[s] = real ? gamma_cm(p, rr.x - qx, rr.y - qy, 0.0f) : 0.0f;
@@ -475,7 +548,7 @@ __device__ __forceinline__ void okrige_solve_block(const HashView& h, const Grid
         const int ea = 30 - exp_above(fmaxf(1.0f, 2.0f * gmax));
         const float sa = pow2f(ea);
 #pragma unroll
-        for (int s = 0; s < kR; ++s) T[4 * (G * s + t) + 2] = gr0[s] * sa;  // Gamma_r0, fixed-point scale
+        for (int s = 0; s < kR; ++s) T[2 * K + G * s + t] = gr0[s] * sa;  // Gamma_r0, fixed-point scale
         const ScaledVgm sv = scaled_vgm(p, sa);
         __syncwarp();
 
@@ -511,6 +584,40 @@ __device__ __forceinline__ void okrige_solve_block(const HashView& h, const Grid
             constexpr bool kSph = decltype(spherical)::value;
 #pragma unroll
             for (int q = 0; q < kR; ++q) {
+                const int c = t + G * q;
+                const float4 cc = rec(c);
+                const float xc = cc.x, yc = cc.y, gcc = cc.z;
+                if constexpr (G >= 4) {
+                    // the diagonal block: entry (t + d mod G, t) of this thread's
+                    // column for d = 1 .. G/2 (d = G/2 only for t < G/2, so each
+                    // pair of the block is taken once), evaluated with the
+                    // other row's record and stored at its lower-triangle place;
+                    // the value is symmetric, bit for bit, in the two records
+                    constexpr int kH = G / 2;
+                    float dv[kH];
+                    int ri[kH];
+#pragma unroll
+                    for (int d = 1; d <= kH; ++d) ri[d - 1] = G * q + (t + d) % G;
+                    if constexpr (kSph) {
+#pragma unroll
+                        for (int d = 0; d < kH; d += 2)
+                            gamma_rows2_sph(sv, T[ri[d]], T[ri[d + 1]], T[K + ri[d]], T[K + ri[d + 1]],
+                                            T[2 * K + ri[d]], T[2 * K + ri[d + 1]], xc, yc, gcc,
+                                            dv[d], dv[d + 1]);
+                    } else {
+#pragma unroll
+                        for (int d = 0; d < kH; ++d)
+                            dv[d] = (T[2 * K + ri[d]] + gcc) -
+                                    gamma_pair_scaled<false>(sv, T[ri[d]] - xc, T[K + ri[d]] - yc);
+                    }
+                    Aq[tri(c) + c] = __float2int_rn((c + 1 < ke) ? 2.0f * gcc : sa);
+#pragma unroll
+                    for (int d = 0; d < kH; ++d) {
+                        if (d + 1 == kH && t >= kH) break;  // the other half takes these
+                        const int hi = max(ri[d], c), lo = min(ri[d], c);
+                        Aq[tri(hi) + lo] = __float2int_rn((hi + 1 < ke) ? dv[d] : 0.0f);
+                    }
+                } else {
                 float dv[kDiagSlots];
 #pragma unroll
                 for (int m = 0; m < kDiagSlots; ++m)
@@ -521,15 +628,25 @@ __device__ __forceinline__ void okrige_solve_block(const HashView& h, const Grid
                 for (int m = 0; m < kDiagSlots; ++m)
                     if (kDiag % G == 0 || m + 1 < kDiagSlots || t + G * m < kDiag)
                         Aq[tri(G * q + (dij[m] >> 8)) + G * q + (dij[m] & 0xff)] = __float2int_rn(dv[m]);
-                const int c = t + G * q;
-                const float4 cc = rec(c);
-                const float xc = cc.x, yc = cc.y, gcc = cc.z;
+                }
                 constexpr int kB = 4;
 #pragma unroll
                 for (int r0 = G * (q + 1); r0 < K; r0 += kB) {
                     // (K - G (q + 1) need not be a multiple of kB: rows from K on
                     // are skipped at compile time)
                     float vb[kB];
+                    if constexpr (G >= 4 && kSph) {
+                        // r0 is a multiple of 4: rows r0 .. r0 + 3 in one vector per
+                        // array, two rows per packed operation
+                        const float4 X = *reinterpret_cast<const float4*>(T + r0);
+                        const float4 Y = *reinterpret_cast<const float4*>(T + K + r0);
+                        const float4 Z = *reinterpret_cast<const float4*>(T + 2 * K + r0);
+                        gamma_rows2_sph(sv, X.x, X.y, Y.x, Y.y, Z.x, Z.y, xc, yc, gcc, vb[0], vb[1]);
+                        gamma_rows2_sph(sv, X.z, X.w, Y.z, Y.w, Z.z, Z.w, xc, yc, gcc, vb[2], vb[3]);
+#pragma unroll
+                        for (int u = 0; u < kB; ++u)
+                            if (!(r0 + u + 1 < ke)) vb[u] = 0.0f;
+                    } else {
 #pragma unroll
                     for (int u = 0; u < kB; ++u) {
                         const int r = r0 + u;
@@ -539,6 +656,7 @@ __device__ __forceinline__ void okrige_solve_block(const HashView& h, const Grid
                             if (r + 1 < ke)
                                 vb[u] = (a.z + gcc) - gamma_pair_scaled<kSph>(sv, a.x - xc, a.y - yc);
                         }
+                    }
                     }
 #pragma unroll
                     for (int u = 0; u < kB; ++u)
@@ -563,8 +681,8 @@ __device__ __forceinline__ void okrige_solve_block(const HashView& h, const Grid
             b[s] = (r + 1 < ke) ? (gr0[s] + g00) - g0r[s] : 0.0f;
             // the tables are free after assembly: keep the row's output terms
             // there rather than in registers through the solve
-            T[4 * r] = zr[s] - z0;
-            T[4 * r + 1] = g0r[s] - gr0[s];
+            T[r] = zr[s] - z0;
+            T[K + r] = g0r[s] - gr0[s];
 #pragma unroll
             for (int c = 0; c < G * (s + 1); ++c) {
                 const int q = Aq[c <= r ? tri(r) + c : 0];
@@ -660,8 +778,8 @@ __device__ __forceinline__ void okrige_solve_block(const HashView& h, const Grid
             const bool row = G * s + t + 1 < ke;
             const float lam = row ? x[s] : 0.0f;
             ps += lam;
-            pz = fmaf(lam, T[4 * (G * s + t)], pz);      // z_a - z_0
-            pv = fmaf(lam, T[4 * (G * s + t) + 1], pv);  // gamma_0a - Gamma_a0
+            pz = fmaf(lam, T[G * s + t], pz);      // z_a - z_0
+            pv = fmaf(lam, T[K + G * s + t], pv);  // gamma_0a - Gamma_a0
         }
         double wsum = (double)ps;
 #pragma unroll
