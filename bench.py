@@ -73,11 +73,14 @@ def knn_int_ops_per_node(k):
 
 HASH_BYTES_PER_SOUNDING = 36.0
 
-# DRAM bytes (read + write) per node of k_okrige_solve<32> with the fused IDW,
-# from one ncu capture of the current kernel on the 2-line swath (3.384M
-# nodes: 450.4 MB read + 38.3 MB written per launch, mostly the 128 B of
-# neighbour ids per node); traffic grows with the nodes of a launch.
-SOLVE_DRAM_BYTES_PER_NODE = (452.216064e6 + 38.499584e6) / 3.384e6
+# DRAM bytes (read + write) per node, from one ncu capture of each kernel on
+# the 2-line swath (3.384M nodes, one launch); traffic grows with the nodes of
+# a launch:
+#  - k_okrige_solve<32> with the fused IDW: 451.0 MB read + 38.7 MB written,
+#    mostly the 128 B of neighbour ids per node;
+#  - k_knn_ids<32>: 19.4 MB read + 378.1 MB written (the ids).
+SOLVE_DRAM_BYTES_PER_NODE = (451.004416e6 + 38.697984e6) / 3.384e6
+KNN_DRAM_BYTES_PER_NODE = (19.4e6 + 378.1e6) / 3.384e6
 
 
 def load_peaks():
