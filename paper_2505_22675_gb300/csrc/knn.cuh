@@ -258,7 +258,10 @@ __device__ __forceinline__ int knn_scan(const HashView& h, int qx, int qy, const
 // so the warp's accesses never share a bank whatever the heap positions).
 // Inserting into a full heap replaces the root and sifts it down: O(log K)
 // instead of the O(K) compare-select chain of a sorted register array, which
-// SIMT pays for whenever any lane of the warp inserts.
+// SIMT pays for whenever any lane of the warp inserts. The heap fills by
+// pushes (sift-up from the new leaf, about two levels on average): one heap
+// build when the K-th key arrives would run at a different candidate in
+// every lane, and the warp would execute all 32 builds one after another.
 
 template <int S>
 __device__ __forceinline__ void heap_sift_down(uint64_t* hp, int i, int n, uint64_t v) {
@@ -281,9 +284,18 @@ __device__ __forceinline__ void heap_sift_down(uint64_t* hp, int i, int n, uint6
     hp[i * S] = v;
 }
 
+// Push v onto a max-heap of n keys (stride S): sift up from the new leaf.
 template <int S>
-__device__ __forceinline__ void heap_build(uint64_t* hp, int n) {
-    for (int i = n / 2 - 1; i >= 0; --i) heap_sift_down<S>(hp, i, n, hp[i * S]);
+__device__ __forceinline__ void heap_push(uint64_t* hp, int n, uint64_t v) {
+    int i = n;
+    while (i > 0) {
+        const int p = (i - 1) >> 1;
+        const uint64_t pv = hp[p * S];
+        if (pv >= v) break;
+        hp[i * S] = pv;
+        i = p;
+    }
+    hp[i * S] = v;
 }
 
 // Phase 2 with the heap. On return hp[0 .. keff) holds the neighbours' packed
@@ -342,11 +354,8 @@ __device__ __forceinline__ int knn_scan_heap_rt(const HashView& h, int qx, int q
             const uint64_t c = (d2 << bits) | (uint32_t)v.w;
             if (c < root) {
                 if (cnt < kc) {
-                    hp[cnt * S] = c;
-                    if (++cnt == kc) {
-                        heap_build<S>(hp, kc);
-                        root = hp[0];
-                    }
+                    heap_push<S>(hp, cnt, c);
+                    if (++cnt == kc) root = hp[0];
                 } else {
                     heap_sift_down<S>(hp, 0, kc, c);
                     root = hp[0];
@@ -363,7 +372,6 @@ __device__ __forceinline__ int knn_scan_heap_rt(const HashView& h, int qx, int q
         if (p < e) take(__ldg(h.rec + p));
         tau = min(tau, (int64_t)(root >> bits));
     }
-    if (cnt < kc) heap_build<S>(hp, cnt);
     if constexpr (kSort) {  // heapsort into ascending order (else the caller drains the max-heap)
         for (int e = cnt - 1; e > 0; --e) {
             const uint64_t v = hp[e * S];
