@@ -78,9 +78,9 @@ HASH_BYTES_PER_SOUNDING = 36.0
 # a launch:
 #  - k_okrige_solve<32> with the fused IDW: 451.0 MB read + 38.7 MB written,
 #    mostly the 128 B of neighbour ids per node;
-#  - k_knn_ids<32>: 19.4 MB read + 378.1 MB written (the ids).
+#  - k_knn_ids<32>: 20.3 MB read + 379.2 MB written (the ids).
 SOLVE_DRAM_BYTES_PER_NODE = (451.004416e6 + 38.697984e6) / 3.384e6
-KNN_DRAM_BYTES_PER_NODE = (19.4e6 + 378.1e6) / 3.384e6
+KNN_DRAM_BYTES_PER_NODE = (20.303872e6 + 379.212032e6) / 3.384e6
 
 
 def load_peaks():
