@@ -93,6 +93,8 @@ __device__ __forceinline__ int empty_rows_beyond(const HashView& h, int row, int
 struct Bound {
     int64_t tau0;   // d_K^2 <= tau0
     int cy;         // the node's (clamped) cell row
+    int count;      // soundings in the table's square (0: unknown)
+    int64_t area;   // its area in cm^2
 };
 
 // Phase 1: the smallest square around the node's cell holding >= kc soundings.
@@ -133,7 +135,7 @@ __device__ __forceinline__ Bound knn_bound_rt(const HashView& h, int qx, int qy,
     const int64_t yhi = (int64_t)h.hy0 + (int64_t)(yb + 1) * h.cs - 1;
     const int64_t mdx = max((int64_t)qx - xlo, xhi - (int64_t)qx);
     const int64_t mdy = max((int64_t)qy - ylo, yhi - (int64_t)qy);
-    return Bound{mdx * mdx + mdy * mdy, cy};
+    return Bound{mdx * mdx + mdy * mdy, cy, cnt(hi), (xhi - xlo + 1) * (yhi - ylo + 1)};
 }
 
 template <int K>
@@ -462,13 +464,15 @@ __device__ __forceinline__ void knn_strip(const HashView& h, const GridView& g, 
         const int i = i0 + s;
         if (i >= g.nx) break;
         const int qx = g.x0 + i * g.cell + g.cell / 2;
-        Bound b{0, cy};
+        Bound b{0, cy, 0, 0};
         bool ok = false;
         if (prev >= 0) {
             const int64_t r = isqrt_ub(prev) + g.cell;  // >= ceil(d_K(prev)) + |step|
             b.tau0 = r * r;
             ok = packed_fits(h, b.tau0);
         }
+        bool guessed = false;
+        Bound bt = b;
         if (!ok) {
             b = knn_bound_rt(h, qx, qy, kc);
             cy = b.cy;
@@ -477,8 +481,22 @@ __device__ __forceinline__ void knn_strip(const HashView& h, const GridView& g, 
                 prev = -1;
                 continue;
             }
+            // the table's square is loose (its far corner): start instead from
+            // 1.5 times the area that holds K soundings at the square's density.
+            // The search is exact whenever K soundings lie within that bound
+            // (everything within it is visited); otherwise it runs again from
+            // the square's bound.
+            bt = b;
+            if (b.count > 0) {
+                const float tg = 1.5f * (float)kc * (float)b.area / (3.14159265f * (float)b.count);
+                if (tg < (float)b.tau0) {
+                    bt.tau0 = (int64_t)tg;
+                    guessed = true;
+                }
+            }
         }
-        const int cnt = knn_scan_heap_rt<S, kSort>(h, qx, qy, b, hp, kc);
+        int cnt = knn_scan_heap_rt<S, kSort>(h, qx, qy, bt, hp, kc);
+        if (guessed && cnt < kc) cnt = knn_scan_heap_rt<S, kSort>(h, qx, qy, b, hp, kc);
         // the K-th key: the last one when sorted, the root of the heap when not
         prev = cnt == kc ? (int64_t)(hp[(kSort ? kc - 1 : 0) * S] >> h.idx_bits) : -1;
         emit(i, cnt);
@@ -517,7 +535,7 @@ __device__ __forceinline__ void knn_chain(const HashView& h, const int32_t* __re
             prev = -1;
             continue;
         }
-        Bound b{0, 0};
+        Bound b{0, 0, 0, 0};
         bool ok = false;
         if (prev >= 0 && prev < ((int64_t)1 << 60)) {  // r below 2^31 + 4: r * r cannot wrap
             const int64_t dx = (int64_t)qx - qxp, dy = (int64_t)qy - qyp;
