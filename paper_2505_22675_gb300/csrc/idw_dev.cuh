@@ -31,7 +31,8 @@ __device__ __forceinline__ float idw_d2f(uint64_t v) {
 // weight of a neighbour at squared distance di relative to the nearest (d1):
 // (d1 / di)^(p/2), with l1 = log2(d1) and hp = p / 2
 __device__ __forceinline__ float idw_weight(float d1, float l1, float hp, float power, float di) {
-    return (power == 2.0f) ? d1 / di : exp2f(hp * (l1 - log2f(di)));
+    if (power == 2.0f) return d1 / di;
+    return exp2f(hp * (l1 - log2f(di)));
 }
 
 // The sums of an IDW run in one fixed order, so that every kernel that forms
@@ -59,7 +60,8 @@ __device__ __forceinline__ float idw_from(const HashView& h, int keff, float pow
     const float z1 = __int_as_float(__ldg(zb + 4 * (int64_t)i0));
     if (d0 == 0) return z1;  // node on top of a sounding
     const float d1 = idw_d2f(d0);
-    const float l1 = log2f(d1);
+    float l1 = 0.0f;  // log2(d1), for powers other than 2
+    if (power != 2.0f) l1 = log2f(d1);
     const float hp = 0.5f * power;
     float num[kIdwLanes], den[kIdwLanes];
 #pragma unroll

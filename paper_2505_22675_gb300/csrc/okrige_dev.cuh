@@ -190,6 +190,40 @@ __device__ __forceinline__ void gamma_rows2_sph(const ScaledVgm& v, float xa, fl
     upk2(sub2(add2(pk2(za, zb), pk2(gcc, gcc)), gm), oa, ob);
 }
 
+// gamma_pair_f, spherical model, for two rows at once (packed FP32, each lane
+// the scalar operations in the same order)
+__device__ __forceinline__ void gamma_pair_sph2(const OkParams& p, float dxa, float dya, float dxb,
+                                                float dyb, float& ga, float& gb) {
+    const unsigned long long dx = pk2(dxa, dxb), dy = pk2(dya, dyb);
+    const unsigned long long d2 = fma2(dx, dx, mul2(dy, dy));
+    float ea, eb;
+    upk2(add2(d2, pk2(1e-30f, 1e-30f)), ea, eb);
+    const unsigned long long h = mul2(d2, pk2(rsqrtf(ea), rsqrtf(eb)));
+    float ta, tb;
+    upk2(mul2(mul2(h, pk2(p.inv_a, p.inv_a)), pk2(0.01f, 0.01f)), ta, tb);
+    const unsigned long long t = pk2(fminf(ta, 1.0f), fminf(tb, 1.0f));
+    const unsigned long long in = fma2(mul2(pk2(-0.5f, -0.5f), t), t, pk2(1.5f, 1.5f));
+    upk2(fma2(mul2(pk2(p.c, p.c), t), in, pk2(p.c0, p.c0)), ga, gb);
+}
+
+// gamma_cm (zero separation gives 0), spherical model, for two rows at once
+__device__ __forceinline__ void gamma_cm_sph2(const OkParams& p, int dxa, int dya, int dxb, int dyb,
+                                              float& ga, float& gb) {
+    const unsigned long long fx = pk2((float)dxa, (float)dxb), fy = pk2((float)dya, (float)dyb);
+    const unsigned long long d2 = fma2(fx, fx, mul2(fy, fy));
+    float da, db;
+    upk2(d2, da, db);
+    float ta, tb;
+    upk2(mul2(mul2(mul2(d2, pk2(rsqrtf(da), rsqrtf(db))), pk2(0.01f, 0.01f)), pk2(p.inv_a, p.inv_a)),
+         ta, tb);
+    const unsigned long long t = pk2(ta, tb);
+    const unsigned long long in = fma2(mul2(pk2(-0.5f, -0.5f), t), t, pk2(1.5f, 1.5f));
+    float va, vb;
+    upk2(fma2(mul2(pk2(p.c, p.c), t), in, pk2(p.c0, p.c0)), va, vb);
+    ga = ((dxa | dya) == 0) ? 0.0f : (ta >= 1.0f ? p.sill : va);
+    gb = ((dxb | dyb) == 0) ? 0.0f : (tb >= 1.0f ? p.sill : vb);
+}
+
 // ------------------------------------------------------------ k-NN -> ids
 
 template <int K, bool kWide>
@@ -487,6 +521,9 @@ __device__ __forceinline__ void okrige_solve_block(const HashView& h, const Grid
         const float z0 = __int_as_float(r0.z);
         const float g00 = gamma_cm(p, r0.x - qx, r0.y - qy, 0.0f);
         float zr[kR], gr0[kR], g0r[kR];  // depth; Gamma(row's neighbour, nbr 0); gamma(node, row's nbr)
+        float pox[kR], poy[kR];  // row's offsets from neighbour 0 (cm)
+        int pdx[kR], pdy[kR];    // and from the node
+        bool preal[kR];
         float gmax = 0.0f;
         // fused IDW: squared distance to the nearest, and each row's weight and anomaly
         uint64_t idw_d0 = 0;
@@ -495,7 +532,7 @@ __device__ __forceinline__ void okrige_solve_block(const HashView& h, const Grid
             const long long dx = (long long)r0.x - qx, dy = (long long)r0.y - qy;
             idw_d0 = (uint64_t)(dx * dx + dy * dy);
             idw_d1 = idw_d2f(idw_d0);
-            idw_l1 = log2f(idw_d1);
+            if (fz.power != 2.0f) idw_l1 = log2f(idw_d1);
         }
 #pragma unroll
         for (int s = 0; s < kR; ++s) {
@@ -516,10 +553,34 @@ __device__ __forceinline__ void okrige_solve_block(const HashView& h, const Grid
             T[r] = ox;
             T[K + r] = oy;
             zr[s] = __int_as_float(rr.z);
-            gr0[s] = real ? gamma_pair_f(p, ox, oy) : 0.0f;
-            g0r[s] = real ? gamma_cm(p, rr.x - qx, rr.y - qy, 0.0f) : 0.0f;
-            gmax = fmaxf(gmax, gr0[s]);
+            pox[s] = ox;
+            poy[s] = oy;
+            pdx[s] = rr.x - qx;
+            pdy[s] = rr.y - qy;
+            preal[s] = real;
         }
+        if (p.model == BG_VARIOGRAM_SPHERICAL && kR % 2 == 0) {
+            // two rows per packed instruction: the same operations as
+            // gamma_pair_f and gamma_cm, lane by lane
+#pragma unroll
+            for (int s = 0; s < kR; s += 2) {
+                float ga, gb, ha, hb;
+                gamma_pair_sph2(p, pox[s], poy[s], pox[s + 1], poy[s + 1], ga, gb);
+                gamma_cm_sph2(p, pdx[s], pdy[s], pdx[s + 1], pdy[s + 1], ha, hb);
+                gr0[s] = preal[s] ? ga : 0.0f;
+                gr0[s + 1] = preal[s + 1] ? gb : 0.0f;
+                g0r[s] = preal[s] ? ha : 0.0f;
+                g0r[s + 1] = preal[s + 1] ? hb : 0.0f;
+            }
+        } else {
+#pragma unroll
+            for (int s = 0; s < kR; ++s) {
+                gr0[s] = preal[s] ? gamma_pair_f(p, pox[s], poy[s]) : 0.0f;
+                g0r[s] = preal[s] ? gamma_cm(p, pdx[s], pdy[s], 0.0f) : 0.0f;
+            }
+        }
+#pragma unroll
+        for (int s = 0; s < kR; ++s) gmax = fmaxf(gmax, gr0[s]);
 #pragma unroll
         for (int o = 1; o < G; o <<= 1) gmax = fmaxf(gmax, __shfl_xor_sync(kFull, gmax, o));
         if constexpr (kIdw) {
