@@ -371,10 +371,18 @@ __device__ __forceinline__ void chol_column(float (&L)[Geo<K>::LEN], float (&din
     }
 }
 
+// The factorization also runs the first solve's forward sweep: column J's
+// step of L y = v right after column J is final, the same operations in the
+// same order as the separate sweep, in the latency gaps of the factorization.
+template <int K, int J>
+__device__ __forceinline__ void fwd_step(const float (&L)[Geo<K>::LEN], const float (&dinv)[kR],
+                                         float (&v)[kR], int t, int gbase);
+
 template <int K, int... J>
 __device__ __forceinline__ void chol_factor(float (&L)[Geo<K>::LEN], float (&dinv)[kR], int t,
-                                            int gbase, float* cb, std::integer_sequence<int, J...>) {
-    (chol_column<K, J>(L, dinv, t, gbase, cb), ...);
+                                            int gbase, float* cb, float (&v)[kR],
+                                            std::integer_sequence<int, J...>) {
+    ((chol_column<K, J>(L, dinv, t, gbase, cb), fwd_step<K, J>(L, dinv, v, t, gbase)), ...);
 }
 
 // forward sweep step j of L y = v (L rows in registers)
@@ -442,8 +450,8 @@ __device__ __forceinline__ void bwd_step(const float (&L)[Geo<K>::LEN], const fl
 template <int K, int kLook, int... J>
 __device__ __forceinline__ void chol_solve_seq(const float (&L)[Geo<K>::LEN],
                                                const float (&dinv)[kR], float (&v)[kR], int t,
-                                               int gbase, std::integer_sequence<int, J...>) {
-    (fwd_step<K, J>(L, dinv, v, t, gbase), ...);
+                                               int gbase, bool fwd, std::integer_sequence<int, J...>) {
+    if (fwd) (fwd_step<K, J>(L, dinv, v, t, gbase), ...);  // else done in the factorization
     float p0 = 0.0f, p1 = 0.0f, e0 = 0.0f;
     (bwd_step<K, kLook, J>(L, dinv, v, t, gbase, p0, p1, e0), ...);
 }
@@ -755,18 +763,19 @@ __device__ __forceinline__ void okrige_solve_block(const HashView& h, const Grid
         float dinv[kR];
 #pragma unroll
         for (int s = 0; s < kR; ++s) dinv[s] = 1.0f;
-        chol_factor<K>(L, dinv, t, gbase, sysmem + Gm::CB, std::make_integer_sequence<int, K>{});
+        float v[kR], x[kR];
+#pragma unroll
+        for (int s = 0; s < kR; ++s) v[s] = b[s] * sa;
+        chol_factor<K>(L, dinv, t, gbase, sysmem + Gm::CB, v, std::make_integer_sequence<int, K>{});
 
         // solve, one refinement step, solve again. The residual b - A' x' is
         // exact: x' is x rounded to 24-bit fixed point (representable in FP32),
         // A' the 30-bit copy, and the sum of the 2^54-bounded products is
         // accumulated in 64-bit integers without rounding.
-        float v[kR], x[kR];
-#pragma unroll
-        for (int s = 0; s < kR; ++s) v[s] = b[s] * sa;
 #pragma unroll 1
         for (int pass = 0; pass < 2; ++pass) {
-            chol_solve_seq<K, kBwdLook>(L, dinv, v, t, gbase, std::make_integer_sequence<int, K>{});
+            chol_solve_seq<K, kBwdLook>(L, dinv, v, t, gbase, pass != 0,
+                                        std::make_integer_sequence<int, K>{});
             if (pass == 1) {
 #pragma unroll
                 for (int s = 0; s < kR; ++s) x[s] += v[s];
