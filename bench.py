@@ -1021,7 +1021,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-nodes", type=int, default=50_000, help="reference arm: nodes per step")
-    ap.add_argument("--serving-tiles", type=int, default=1000,
+    ap.add_argument("--serving-tiles", type=int, default=2000,
                     help="tiles per arrival rate of the serving sweep (50-2000 tiles/s)")
     ap.add_argument("--serving-pool", type=int, default=48)
     ap.add_argument("--no-serving", action="store_true")
