@@ -30,6 +30,12 @@
 //     sigma^2 = lambda_0 gamma_00 + sum_a lambda_a gamma_a0 + mu.
 // Rows beyond k_eff - 1 are identity rows with zero right-hand side, so every
 // system has the fixed size K and all loops over rows and columns unroll.
+// Much of the FP32 work runs as packed two-lane instructions (add/sub/mul/fma
+// .rn.f32x2: one instruction, two IEEE single operations, each lane rounded
+// as its scalar form): the variogram assembly two rows at a time, the per-row
+// variograms of the prologue, and column pairs of the Cholesky update. The
+// solve is issue- and latency-bound, so halving those instructions pays, and
+// the results are bitwise those of the scalar code.
 #pragma once
 
 #include <algorithm>
@@ -624,12 +630,13 @@ __device__ __forceinline__ void okrige_solve_block(const HashView& h, const Grid
         // assemble the lower triangle once per entry, straight into fixed
         // point. Every term is in the fixed-point scale already (the records'
         // Gamma_r0 and the scaled variogram), so an entry is one rounding to
-        // integer. The
-        // triangle splits into G x G blocks: below the diagonal blocks,
-        // thread t owns the columns c = t + G q and the group walks the rows
-        // in step (a row's entries land in consecutive banks); the
-        // G (G + 1) / 2 entries of a diagonal block are dealt out to the
-        // group's threads in turn, so no thread idles above its column.
+        // integer. The triangle splits into G x G blocks: below the diagonal
+        // blocks, thread t owns the columns c = t + G q and the group walks
+        // the rows in step (a row's entries land in consecutive banks), four
+        // rows per batch, two per packed instruction. With G >= 4 a diagonal
+        // block is taken by a circulant assignment in each thread's own
+        // column (below); smaller groups deal its G (G + 1) / 2 entries out to
+        // the group's threads in turn.
         auto entry_value = [&](auto spherical, int r, int c) {
             constexpr bool kSph = decltype(spherical)::value;
             const float4 a = rec(r), b = rec(c);
