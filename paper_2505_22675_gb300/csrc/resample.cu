@@ -87,16 +87,17 @@ __device__ __forceinline__ void cr_weights(float t, float (&w)[4]) {
     w[3] = 0.5f * (t3 - t2);
 }
 
-// One query from its two axes. rows[b] points at source row j - 1 + b
-// (clamped into the grid; bilinear uses rows[1] and rows[2]). Only the
+// One query from its two axes. fetch(b, c) returns the source node at column
+// c (clamped into the grid by the caller) of stencil row b, i.e. source row
+// j - 1 + b clamped into the grid (bilinear uses rows 1 and 2). Only the
 // needed stencil nodes are read (predicated loads, no branches), so the loads
 // of a thread's queries overlap. how: 0 by the method, 1 by the bilinear
 // fallback, 2 no value.
 // kColX: every query of the launch lies on a node column (the row-filling
 // shape), so only the column case is compiled.
-template <int kMethod, bool kColX = false>
+template <int kMethod, bool kColX, class Fetch>
 __device__ __forceinline__ float resample_at(const Src& s, const Axis& ax, const Axis& ay,
-                                             const float* const (&rows)[4], int8_t& how) {
+                                             const Fetch& fetch, int8_t& how) {
     float f;
     const int i = ax.i;
     if constexpr (kMethod == BG_RESAMPLE_CATMULL_ROM) {
@@ -110,7 +111,7 @@ __device__ __forceinline__ float resample_at(const Src& s, const Axis& ax, const
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
                 ny_[b] = needed(ay, s.cell, b);
-                P[b] = ny_[b] ? __ldg(rows[b] + c) : 0.0f;
+                P[b] = ny_[b] ? fetch(b, c) : 0.0f;
             }
             const float ref = P[ay.r == s.cell ? 2 : 1];
             float wy[4];
@@ -144,7 +145,7 @@ __device__ __forceinline__ float resample_at(const Src& s, const Axis& ax, const
             for (int b = 0; b < 4; ++b)
 #pragma unroll
                 for (int a = 0; a < 4; ++a)
-                    P[b][a] = (nx_[a] && ny_[b]) ? __ldg(rows[b] + col[a]) : 0.0f;
+                    P[b][a] = (nx_[a] && ny_[b]) ? fetch(b, col[a]) : 0.0f;
             const float ref = P[ay.r == s.cell ? 2 : 1][ax.r == s.cell ? 2 : 1];
             float wx[4], wy[4];
             cr_weights(frac_of(ax.r, s), wx);
@@ -174,10 +175,10 @@ __device__ __forceinline__ float resample_at(const Src& s, const Axis& ax, const
         }
     } else {
         const bool x0 = ax.r != s.cell, x1 = ax.r != 0, y0 = ay.r != s.cell, y1 = ay.r != 0;
-        const float q00 = (x0 && y0) ? __ldg(rows[1] + i) : 0.0f;
-        const float q10 = (x1 && y0) ? __ldg(rows[1] + i + 1) : 0.0f;
-        const float q01 = (x0 && y1) ? __ldg(rows[2] + i) : 0.0f;
-        const float q11 = (x1 && y1) ? __ldg(rows[2] + i + 1) : 0.0f;
+        const float q00 = (x0 && y0) ? fetch(1, i) : 0.0f;
+        const float q10 = (x1 && y0) ? fetch(1, i + 1) : 0.0f;
+        const float q01 = (x0 && y1) ? fetch(2, i) : 0.0f;
+        const float q11 = (x1 && y1) ? fetch(2, i + 1) : 0.0f;
         f = bilinear_from(s, ax, ay, q00, q10, q01, q11);
         how = isnan(f) ? 2 : 0;
     }
@@ -213,8 +214,9 @@ __global__ void __launch_bounds__(kThreads) k_resample_pts(Src s, const int32_t*
             const Axis ay = axis_of((int64_t)__ldg(qy + pc) - s.cy0, s.cell, s.ny);
             const float* rows[4];
             row_ptrs(s, ay.i, rows);
+            const auto fetch = [&](int b, int c) { return __ldg(rows[b] + c); };
             int8_t how;
-            const float f = resample_at<kMethod>(s, ax, ay, rows, how);
+            const float f = resample_at<kMethod, false>(s, ax, ay, fetch, how);
             if (p < m) {
                 out[p] = f;
                 if (how_out) how_out[p] = how;
@@ -229,7 +231,7 @@ __global__ void __launch_bounds__(kThreads) k_resample_pts(Src s, const int32_t*
 constexpr int kRowsPerBlock = 8;
 
 template <int kMethod, bool kColX>
-__global__ void __launch_bounds__(kThreads, kMethod == BG_RESAMPLE_CATMULL_ROM ? 4 : 8)
+__global__ void __launch_bounds__(kThreads, 4)
     k_resample_grid(Src s, GridView o, int chunks, float* __restrict__ out,
                     int8_t* __restrict__ how_out) {
     const int band = blockIdx.x / chunks;
@@ -247,16 +249,127 @@ __global__ void __launch_bounds__(kThreads, kMethod == BG_RESAMPLE_CATMULL_ROM ?
             axis_of((int64_t)o.y0 + (int64_t)row * o.cell + o.cell / 2 - s.cy0, s.cell, s.ny);
         const float* rows[4];
         row_ptrs(s, ay.i, rows);
+        const auto fetch = [&](int b, int c) { return __ldg(rows[b] + c); };
 #pragma unroll
         for (int k = 0; k < kPer; ++k) {
             const int c = c0 + k * kThreads;
             int8_t how;
-            const float f = resample_at<kMethod, kColX>(s, ax[k], ay, rows, how);
+            const float f = resample_at<kMethod, kColX>(s, ax[k], ay, fetch, how);
             if (c < o.nx) {
                 const int64_t p = (int64_t)row * o.nx + c;
                 out[p] = f;
                 if (how_out) how_out[p] = how;
             }
+        }
+    }
+}
+
+// Output grid at the source's own spacing whose columns lie on source columns
+// (output column c on source column c + d; d, both row lengths a multiple of
+// 4 and the arrays 16-byte aligned; the row-filling shape): a thread takes 4
+// consecutive columns in each of kVecGroups places of its band's rows and
+// moves them with 16-byte loads and stores (a 4-byte store of the how-codes);
+// its stencil rows come from those vectors, held in registers. They are
+// loaded exactly when the row's stencil needs them, and a vector lies either
+// wholly inside the source's columns or wholly outside (no value). A row on a
+// source row line takes resample_at's node-column case itself; a row between
+// two takes the same roundings without the selects of zero weights (results
+// equal to k_resample_grid's up to the sign of a zero). This kernel moves
+// 9 B per output (a read of the source row, the value and the how-code) at
+// 1:1 and has few instructions per byte: with 8 (bilinear) or 6 (Catmull-
+// Rom) blocks per SM it runs close to the copy bandwidth.
+constexpr int kVec = 4;
+constexpr int kVecGroups = 1;
+
+__device__ __forceinline__ float lane_of(const float4& v, int k) {
+    return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w));
+}
+
+template <int kMethod>
+__global__ void __launch_bounds__(kThreads, kMethod == BG_RESAMPLE_CATMULL_ROM ? 6 : 8)
+    k_resample_rows(Src s, GridView o, int64_t d, int chunks, float* __restrict__ out,
+                    int8_t* __restrict__ how_out) {
+    const int band = blockIdx.x / chunks;
+    const int cb = (blockIdx.x - band * chunks) * (kThreads * kVec * kVecGroups) + threadIdx.x * kVec;
+    const int64_t uy0 = (int64_t)o.y0 + o.cell / 2 - s.cy0;
+    const int row1 = min(o.ny, (band + 1) * kRowsPerBlock);
+    for (int row = band * kRowsPerBlock; row < row1; ++row) {
+        const Axis ay = axis_of(uy0 + (int64_t)row * o.cell, s.cell, s.ny);
+        const float* rows[4];
+        row_ptrs(s, ay.i, rows);
+        bool use[4];
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+            use[b] = (kMethod == BG_RESAMPLE_CATMULL_ROM || b == 1 || b == 2) && needed(ay, s.cell, b);
+        const bool interior = ay.in && ay.r != 0 && ay.r != s.cell;
+        const float u = frac_of(ay.r, s);
+        float wy[4];
+        cr_weights(u, wy);
+#pragma unroll
+        for (int g = 0; g < kVecGroups; ++g) {
+            const int c = cb + g * kThreads * kVec;
+            if (c >= o.nx) break;
+            const int64_t i0 = c + d;
+            const bool vin = i0 >= 0 && i0 < s.nx;
+            float4 R[4];
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+                R[b] = (vin && use[b]) ? __ldg(reinterpret_cast<const float4*>(rows[b] + i0))
+                                       : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            float f[kVec];
+            int8_t h[kVec];
+            if (interior) {
+                // every stencil row carries weight: resample_at's node-column
+                // arithmetic without its weight-zero selects. Bilinear's terms of
+                // the other column vanish (t is 0 or 1), leaving ref + u (q1 - ref)
+                // with ref = q0, rounded as there; Catmull-Rom's FMA chain is the
+                // same, and a NaN among the four rows is a NaN in the sum of their
+                // magnitudes.
+#pragma unroll
+                for (int k = 0; k < kVec; ++k) {
+                    if constexpr (kMethod == BG_RESAMPLE_CATMULL_ROM) {
+                        const float p0 = lane_of(R[0], k), p1 = lane_of(R[1], k),
+                                    p2 = lane_of(R[2], k), p3 = lane_of(R[3], k);
+                        float acc = fmaf(wy[0], p0 - p1, 0.0f);
+                        acc = fmaf(wy[1], p1 - p1, acc);
+                        acc = fmaf(wy[2], p2 - p1, acc);
+                        acc = fmaf(wy[3], p3 - p1, acc);
+                        if (!isnan(fabsf(p0) + fabsf(p1) + fabsf(p2) + fabsf(p3))) {
+                            f[k] = p1 + acc;
+                            h[k] = 0;
+                        } else {
+                            f[k] = __fadd_rn(p1, __fmul_rn(u, __fsub_rn(p2, p1)));
+                            h[k] = isnan(f[k]) ? 2 : 1;
+                        }
+                    } else {
+                        const float q0 = lane_of(R[1], k), q1 = lane_of(R[2], k);
+                        f[k] = __fadd_rn(q0, __fmul_rn(u, __fsub_rn(q1, q0)));
+                        h[k] = isnan(f[k]) ? 2 : 0;
+                    }
+                    if (!vin) {
+                        f[k] = __int_as_float(0x7fc00000);
+                        h[k] = 2;
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < kVec; ++k) {
+                    // the node column i0 + k as axis_of gives it: cell index clamped
+                    // to nx - 2, remainder 0, or cell on the last column
+                    Axis ax;
+                    ax.in = vin;
+                    ax.i = vin ? (int)min(i0 + k, (int64_t)s.nx - 2) : 0;
+                    ax.r = (vin && i0 + k == s.nx - 1) ? s.cell : 0;
+                    const auto fetch = [&](int b, int) { return lane_of(R[b], k); };
+                    f[k] = resample_at<kMethod, true>(s, ax, ay, fetch, h[k]);
+                }
+            }
+            const int64_t p = (int64_t)row * o.nx + c;
+            *reinterpret_cast<float4*>(out + p) = make_float4(f[0], f[1], f[2], f[3]);
+            if (how_out)
+                *reinterpret_cast<uint32_t*>(how_out + p) =
+                    (uint32_t)(uint8_t)h[0] | (uint32_t)(uint8_t)h[1] << 8 |
+                    (uint32_t)(uint8_t)h[2] << 16 | (uint32_t)(uint8_t)h[3] << 24;
         }
     }
 }
@@ -284,15 +397,36 @@ bg_status launch_resample_points(const float* src, const GridView& g, int method
 bg_status launch_resample_grid(const float* src, const GridView& g, int method, const GridView& o,
                                float* out, int8_t* how, cudaStream_t st) {
     const Src s{src, g.x0 + g.cell / 2, g.y0 + g.cell / 2, g.cell, g.nx, g.ny, 1.0f / (float)g.cell};
+    // output columns on node columns of the source: the column case only
+    const int64_t off = (int64_t)o.x0 + o.cell / 2 - s.cx0;
+    const bool colx = o.cell % s.cell == 0 && ((off % s.cell) + s.cell) % s.cell == 0;
+    const int64_t d = off / s.cell;  // source column of output column 0, when colx
+    if (colx && o.cell == s.cell && ((d % kVec) + kVec) % kVec == 0 && g.nx % kVec == 0 &&
+        o.nx % kVec == 0 && (uintptr_t)src % 16 == 0 && (uintptr_t)out % 16 == 0 &&
+        (uintptr_t)how % 4 == 0) {
+        const int per = kThreads * kVec * kVecGroups;
+        const int chunks = (o.nx + per - 1) / per;
+        const int64_t blocks = (int64_t)chunks * ((o.ny + kRowsPerBlock - 1) / kRowsPerBlock);
+        if (blocks >= ((int64_t)1 << 31)) {
+            set_error("output grid too large for one launch");
+            return BG_ERR_INVALID_ARG;
+        }
+        if (method == BG_RESAMPLE_CATMULL_ROM)
+            k_resample_rows<BG_RESAMPLE_CATMULL_ROM><<<(unsigned)blocks, kThreads, 0, st>>>(
+                s, o, d, chunks, out, how);
+        else
+            k_resample_rows<BG_RESAMPLE_BILINEAR><<<(unsigned)blocks, kThreads, 0, st>>>(
+                s, o, d, chunks, out, how);
+        note_launches(1);
+        BG_CUDA(cudaGetLastError());
+        return BG_OK;
+    }
     const int chunks = (o.nx + kThreads * kPer - 1) / (kThreads * kPer);
     const int64_t blocks = (int64_t)chunks * ((o.ny + kRowsPerBlock - 1) / kRowsPerBlock);
     if (blocks >= ((int64_t)1 << 31)) {
         set_error("output grid too large for one launch");
         return BG_ERR_INVALID_ARG;
     }
-    // output columns on node columns of the source: the column case only
-    const int64_t off = (int64_t)o.x0 + o.cell / 2 - s.cx0;
-    const bool colx = o.cell % s.cell == 0 && ((off % s.cell) + s.cell) % s.cell == 0;
     const unsigned nb = (unsigned)blocks;
     if (method == BG_RESAMPLE_CATMULL_ROM) {
         if (colx)
@@ -300,10 +434,7 @@ bg_status launch_resample_grid(const float* src, const GridView& g, int method, 
         else
             k_resample_grid<BG_RESAMPLE_CATMULL_ROM, false><<<nb, kThreads, 0, st>>>(s, o, chunks, out, how);
     } else {
-        if (colx)
-            k_resample_grid<BG_RESAMPLE_BILINEAR, true><<<nb, kThreads, 0, st>>>(s, o, chunks, out, how);
-        else
-            k_resample_grid<BG_RESAMPLE_BILINEAR, false><<<nb, kThreads, 0, st>>>(s, o, chunks, out, how);
+        k_resample_grid<BG_RESAMPLE_BILINEAR, false><<<nb, kThreads, 0, st>>>(s, o, chunks, out, how);
     }
     note_launches(1);
     BG_CUDA(cudaGetLastError());

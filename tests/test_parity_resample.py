@@ -105,3 +105,71 @@ def test_two_by_two_source_and_empty_lists():
     with pytest.raises(bg.BGError):
         bg.resample_points(_dev(src), (0, 0, 201, 2, 2), 0, _dev(qx, np.int32), _dev(qy, np.int32),
                            torch.empty(qx.size, device="cuda:0"))
+
+
+@pytest.mark.parametrize("method", METHODS)
+def test_output_grids_of_every_shape(method):
+    """Output grids off the source lattice at the same cell, at half and at
+    three times the cell (stencils that skip source columns), one wholly
+    outside the hull, and a 2 x 2 source gridded at a quarter cell."""
+    import torch
+
+    import paper_2505_22675_gb300 as bg
+    h = synth.hole_grid(seed=47, nx=301, ny=75, cell_cm=400, frac=0.03, x0_cm=10_000, y0_cm=-8_000)
+    src = h.source()
+    g = h.grid
+    spec = (g.x0_cm, g.y0_cm, g.cell_cm, g.nx, g.ny)
+    cases = [
+        (src, spec, (g.x0_cm + 150, g.y0_cm + 66, g.cell_cm, g.nx - 1, g.ny - 1)),
+        (src, spec, (g.x0_cm - 1_000, g.y0_cm + 250, g.cell_cm // 2, 2 * g.nx + 9, 2 * g.ny + 3)),
+        (src, spec, (g.x0_cm + 37 * 2, g.y0_cm - 100, 3 * g.cell_cm + 2, g.nx // 3 + 2, g.ny // 3 + 2)),
+        (src, spec, (g.x0_cm + 10_000_000, g.y0_cm, g.cell_cm, 50, 40)),
+        (np.array([3500.0, 3510.0, 3520.0, np.nan], np.float32), (0, 0, 200, 2, 2),
+         (-100, -50, 50, 13, 11)),
+    ]
+    for s_arr, s_spec, out_spec in cases:
+        m = out_spec[3] * out_spec[4]
+        out = torch.full((m,), -7.0, device="cuda:0")
+        how = torch.full((m,), 9, dtype=torch.int8, device="cuda:0")
+        bg.resample_grid(_dev(s_arr), s_spec, method, out_spec, out, how)
+        torch.cuda.synchronize()
+        qx, qy = oracle.grid_nodes(*out_spec)
+        ref, rhow = oracle.resample(s_arr, s_spec, qx, qy, method)
+        _compare(out.cpu().numpy(), how.cpu().numpy(), ref, rhow)
+
+
+@pytest.mark.parametrize("method", METHODS)
+def test_row_filling_in_vectors(method):
+    """Output grids at the source's own spacing on its node columns, rows a
+    multiple of 4 long: the 16-byte vector path. Row midpoints, a grid shifted
+    by 8 columns that overhangs both ends (whole vectors outside the hull) and
+    rows above and below, the last source column (remainder = cell), and the
+    same without how-codes (values bitwise equal)."""
+    import torch
+
+    import paper_2505_22675_gb300 as bg
+    h = synth.hole_grid(seed=53, nx=256, ny=61, cell_cm=400, frac=0.04, x0_cm=-3_000, y0_cm=7_000)
+    src = h.source()
+    g = h.grid
+    c = g.cell_cm
+    spec = (g.x0_cm, g.y0_cm, c, g.nx, g.ny)
+    cases = [
+        (g.x0_cm, g.y0_cm + c // 2, c, g.nx, g.ny - 1),
+        (g.x0_cm - 8 * c, g.y0_cm - 3 * c // 2, c, g.nx + 16, g.ny + 5),
+        (g.x0_cm + 4 * c, g.y0_cm + 130, c, 2048 + 8, 9),
+    ]
+    dsrc = _dev(src)
+    for out_spec in cases:
+        m = out_spec[3] * out_spec[4]
+        out = torch.full((m,), -7.0, device="cuda:0")
+        how = torch.full((m,), 9, dtype=torch.int8, device="cuda:0")
+        bg.resample_grid(dsrc, spec, method, out_spec, out, how)
+        out2 = torch.full((m,), -7.0, device="cuda:0")
+        bg.resample_grid(dsrc, spec, method, out_spec, out2)
+        torch.cuda.synchronize()
+        qx, qy = oracle.grid_nodes(*out_spec)
+        ref, rhow = oracle.resample(src, spec, qx, qy, method)
+        _compare(out.cpu().numpy(), how.cpu().numpy(), ref, rhow)
+        a, b = out.cpu().numpy(), out2.cpu().numpy()
+        assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
+        assert (rhow == 2).any() and (rhow != 2).any()
