@@ -292,9 +292,24 @@ __global__ void __launch_bounds__(kThreads, kMethod == BG_RESAMPLE_CATMULL_ROM ?
     const int band = blockIdx.x / chunks;
     const int cb = (blockIdx.x - band * chunks) * (kThreads * kVec * kVecGroups) + threadIdx.x * kVec;
     const int64_t uy0 = (int64_t)o.y0 + o.cell / 2 - s.cy0;
-    const int row1 = min(o.ny, (band + 1) * kRowsPerBlock);
-    for (int row = band * kRowsPerBlock; row < row1; ++row) {
-        const Axis ay = axis_of(uy0 + (int64_t)row * o.cell, s.cell, s.ny);
+    const int row0 = band * kRowsPerBlock;
+    const int row1 = min(o.ny, row0 + kRowsPerBlock);
+    Axis ay = axis_of(uy0 + (int64_t)row0 * o.cell, s.cell, s.ny);
+    float u = frac_of(ay.r, s);
+    float wy[4];
+    cr_weights(u, wy);
+    for (int row = row0; row < row1; ++row) {
+        if (row > row0) {
+            // one source row further: the same remainder while the next cell
+            // index stays below the clamp, else the axis afresh
+            if (ay.in && ay.r < s.cell && ay.i + 1 <= s.ny - 2) {
+                ++ay.i;
+            } else {
+                ay = axis_of(uy0 + (int64_t)row * o.cell, s.cell, s.ny);
+                u = frac_of(ay.r, s);
+                cr_weights(u, wy);
+            }
+        }
         const float* rows[4];
         row_ptrs(s, ay.i, rows);
         bool use[4];
@@ -302,9 +317,6 @@ __global__ void __launch_bounds__(kThreads, kMethod == BG_RESAMPLE_CATMULL_ROM ?
         for (int b = 0; b < 4; ++b)
             use[b] = (kMethod == BG_RESAMPLE_CATMULL_ROM || b == 1 || b == 2) && needed(ay, s.cell, b);
         const bool interior = ay.in && ay.r != 0 && ay.r != s.cell;
-        const float u = frac_of(ay.r, s);
-        float wy[4];
-        cr_weights(u, wy);
 #pragma unroll
         for (int g = 0; g < kVecGroups; ++g) {
             const int c = cb + g * kThreads * kVec;
