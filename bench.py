@@ -17,7 +17,9 @@ so consecutive steps do not run from cache.
 `--impl reference` times the FP64 CPU oracle on a bounded sample of nodes of
 the same workload on the host cores (the only other program of this path).
 Under torchrun every rank grids its own copy of the swath (weak scaling, no
-collective); rank 0 prints one JSON line.
+collective); rank 0 prints one JSON line. Beside it, `slab_split` times the
+one swath split into row slabs across the ranks (strong scaling: each rank
+builds the whole hash and grids its rows).
 """
 from __future__ import annotations
 
@@ -934,6 +936,50 @@ def bench_ours(args):
         os.sched_setaffinity(0, saved_cpus)
     bad = int(torch.isnan(d_idw).sum() + torch.isnan(d_ok).sum())
 
+    # ---- the row-slab split of the one swath (strong scaling): every rank
+    # uploads all soundings and builds the whole hash, then grids only its
+    # slab of rows (distributed.slab_rows); the slabs equal those rows of the
+    # single-GPU grid bitwise. No collective inside the timed steps.
+    slab = None
+    if ws > 1 or args.slab_split:
+        from paper_2505_22675_gb300.distributed import slab_rows
+        j0, j1 = slab_rows(g.ny, ws, rank)
+        sm_ = g.nx * (j1 - j0)
+        sgrid = bg.grid_create(ctx, g.x0_cm, g.y0_cm + j0 * g.cell_cm, g.cell_cm, g.nx,
+                               max(j1 - j0, 1))
+
+        def slab_step():
+            s = bg.soundings_upload(ctx, xd, yd, zd)
+            if j1 > j0:
+                bg.interp_idw_okrige(s, sgrid, IDW_K, IDW_P, OK_K, vgm, d_idw[:sm_], d_ok[:sm_],
+                                     v_ok[:sm_])
+            bg.soundings_destroy(s)
+
+        for _ in range(max(1, args.warmup)):
+            slab_step()
+        torch.cuda.synchronize()
+        barrier()
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        for _ in range(args.steps):
+            slab_step()
+        s1.record(stream)
+        torch.cuda.synchronize()
+        slab_ms = s0.elapsed_time(s1) / args.steps
+        if ws > 1:
+            import torch.distributed as dist
+            t = torch.tensor([slab_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            slab_ms = float(t.item())
+        slab = {"value": m / (slab_ms / 1e3), "unit": "nodes/s", "ms_per_step": slab_ms,
+                "scaling": "strong", "parallelism": f"row slabs x{ws}",
+                "rows_rank0": int(j1 - j0) if rank == 0 else None,
+                "note": "the one swath split into row slabs, one per rank; each rank uploads "
+                        "all soundings and builds the whole hash (no halo), then grids its "
+                        "slab; max over ranks; the slabs stay on their devices"}
+        bg.grid_destroy(sgrid)
+
     # per-result error against the FP64 oracle at sampled nodes of the last step
     errors = None
     if rank == 0 and not args.no_oracle_check:
@@ -969,6 +1015,8 @@ def bench_ours(args):
                     "d2h_bytes_per_step": int(12 * m), "ms_per_step": e2e_ms, "steps": e_steps},
             "gpu_launches": int(launches), "clocks": clocks, "nan_outputs": bad,
         }
+        if slab is not None:
+            out["slab_split"] = slab
         if not args.no_tiles:
             out["tile_configs"] = tile_configs(bg, torch, local, not args.no_oracle_check)
         pool = None
@@ -1036,6 +1084,9 @@ def main():
     ap.add_argument("--check-nodes", type=int, default=100_000,
                     help="random swath nodes compared with the oracle")
     ap.add_argument("--no-tiles", action="store_true", help="skip the two tile workloads")
+    ap.add_argument("--slab-split", action="store_true",
+                    help="also time the row-slab split of the swath at one rank (it always "
+                         "runs under torchrun with more than one rank)")
     args = ap.parse_args()
     if args.impl == "reference":
         bench_reference(args)
