@@ -70,6 +70,10 @@ __global__ void __launch_bounds__(kGridSolveWarps * 32, kGridSolveBlocksPerSM) k
     const int32_t* __restrict__ ids, float* __restrict__ depth, float* __restrict__ var,
     IdwFuse fz) {
     extern __shared__ __align__(16) float smem[];
+    // the ids of a block two waves on (2 blocks per SM): the k-NN kernel wrote
+    // them a launch ago and they have left L2 since
+    prefetch_ids_l2(ids, nodes, k, (int64_t)blockIdx.x + kIdsPrefetchBlocks,
+                    kGridSolveWarps * Geo<K>::SYS * kRounds);
     okrige_solve_block<K, false, kIdw, kGridSolveWarps>(h, g, k, p, node0, nodes, ids, depth, var,
                                                         blockIdx.x, smem, nullptr, nullptr, fz);
 }
@@ -210,6 +214,8 @@ __global__ void __launch_bounds__(kGridSolveWarps * 32, kGridSolveBlocksPerSM) k
     HashView h, PointsView q, int k, OkParams p, int64_t p0, int64_t nodes,
     const int32_t* __restrict__ ids, float* __restrict__ depth, float* __restrict__ var) {
     extern __shared__ __align__(16) float smem[];
+    prefetch_ids_l2(ids, nodes, k, (int64_t)blockIdx.x + kIdsPrefetchBlocks,
+                    kGridSolveWarps * Geo<K>::SYS * kRounds);
     okrige_solve_block<K, true, false, kGridSolveWarps>(h, GridView{}, k, p, p0, nodes, ids, depth,
                                                         var, blockIdx.x, smem, q.x, q.y);
 }

@@ -57,6 +57,8 @@ constexpr int kBwdLook = 2;      // back-sweep pipeline depth (see bwd_step)
 // different phases fetch far fewer distinct instructions than four.
 constexpr int kGridSolveWarps = 8;
 constexpr int kGridSolveBlocksPerSM = 2;
+// solve blocks ahead whose neighbour ids a block prefetches into L2
+constexpr int kIdsPrefetchBlocks = 2 * 152 * kGridSolveBlocksPerSM;
 
 template <int K>
 struct Geo {
@@ -460,6 +462,20 @@ __device__ __forceinline__ void chol_solve_seq(const float (&L)[Geo<K>::LEN],
     if (fwd) (fwd_step<K, J>(L, dinv, v, t, gbase), ...);  // else done in the factorization
     float p0 = 0.0f, p1 = 0.0f, e0 = 0.0f;
     (bwd_step<K, kLook, J>(L, dinv, v, t, gbase, p0, p1, e0), ...);
+}
+
+// L2 prefetch of the neighbour ids of solve block pb (sys systems of k ids
+// each, from ids[pb * sys * k]): warp 0, one 128-byte line per lane, within
+// the `nodes` systems of the launch. A hint that nothing waits on.
+__device__ __forceinline__ void prefetch_ids_l2(const int32_t* ids, int64_t nodes, int k,
+                                                int64_t pb, int sys) {
+    if (threadIdx.x >= 32) return;
+    const int64_t s0 = pb * sys;
+    if (s0 >= nodes) return;
+    const int64_t bytes = min((int64_t)sys, nodes - s0) * k * (int64_t)sizeof(int32_t);
+    const char* base = reinterpret_cast<const char*>(ids + s0 * k);
+    for (int64_t off = (int64_t)threadIdx.x * 128; off < bytes; off += 32 * 128)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(base + off));
 }
 
 // 2^e as a float (|e| <= 126)
