@@ -78,10 +78,10 @@ HASH_BYTES_PER_SOUNDING = 36.0
 # DRAM bytes (read + write) per node, from one ncu capture of each kernel on
 # the 2-line swath (3.384M nodes, one launch); traffic grows with the nodes of
 # a launch:
-#  - k_okrige_solve<32> with the fused IDW: 450.5 MB read + 38.7 MB written,
+#  - k_okrige_solve<32> with the fused IDW: 451.6 MB read + 38.5 MB written,
 #    mostly the 128 B of neighbour ids per node;
 #  - k_knn_ids<32>: 20.1 MB read + 379.2 MB written (the ids).
-SOLVE_DRAM_BYTES_PER_NODE = (450.520576e6 + 38.747648e6) / 3.384e6
+SOLVE_DRAM_BYTES_PER_NODE = (451.642368e6 + 38.503936e6) / 3.384e6
 KNN_DRAM_BYTES_PER_NODE = (20.107264e6 + 379.174144e6) / 3.384e6
 
 

@@ -11,11 +11,14 @@
 // bilinear. Sums are taken as anomalies from one needed node, so at depths of
 // thousands of metres only the final add rounds at that magnitude.
 //
-// A thread takes 4 queries 256 apart and reads the needed stencil nodes of
-// all four with predicated loads, so they overlap; a warp takes 32
-// neighbouring queries, so the source rows it reads are contiguous and
-// shared through L1. The work is a gather bounded by HBM: 4 B per output
-// (+ 8 B of coordinates for point lists), plus one read of the source grid.
+// Point lists and general output grids: a thread takes 4 queries 256 apart
+// and reads the needed stencil nodes of all four with predicated loads, so
+// they overlap; a warp takes 32 neighbouring queries, so the source rows it
+// reads are contiguous and shared through L1. Output grids at the source's
+// spacing on its node columns (the row-filling shape) take k_resample_rows:
+// four columns per thread in 16-byte vectors. The work is a gather bounded
+// by HBM: 4 B per output (+ 8 B of coordinates for point lists), plus one
+// read of the source grid.
 #include <algorithm>
 #include <cmath>
 
