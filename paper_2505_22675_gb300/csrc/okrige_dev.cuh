@@ -57,7 +57,8 @@ constexpr int kBwdLook = 2;      // back-sweep pipeline depth (see bwd_step)
 // different phases fetch far fewer distinct instructions than four.
 constexpr int kGridSolveWarps = 8;
 constexpr int kGridSolveBlocksPerSM = 2;
-// solve blocks ahead whose neighbour ids a block prefetches into L2
+// solve blocks ahead whose neighbour ids a block prefetches into L2: two
+// waves of the 152 SMs (one to eight waves measured the same)
 constexpr int kIdsPrefetchBlocks = 2 * 152 * kGridSolveBlocksPerSM;
 
 template <int K>
