@@ -257,7 +257,8 @@ typedef struct bg_request {
     int32_t k;                 /* neighbours, [1, 32] */
     float power;               /* IDW exponent (> 0) */
     bg_variogram variogram;    /* kriging model */
-    float* depth_out;          /* host, nx*ny, row-major */
+    float* depth_out;          /* host, nx*ny, row-major; contents unspecified
+                                  until the ticket completes with BG_OK */
     float* var_out;            /* host, nx*ny kriging variance, or NULL */
 } bg_request;
 
@@ -278,7 +279,10 @@ typedef struct bg_result {
  * pinned staging, asynchronous upload and kernel launches: tens of
  * microseconds for a typical tile) before returning; otherwise the request is
  * queued for the context's dispatcher thread. A request whose estimate alone
- * exceeds the budget is refused with BG_ERR_OOM_BUDGET. Thread-safe. */
+ * exceeds the budget is refused with BG_ERR_OOM_BUDGET. Thread-safe.
+ * A context that serves runs a dispatcher thread, a completion thread and
+ * three copy-out helper threads; the completion thread and the helpers spin
+ * (yielding) while requests are in flight and sleep otherwise. */
 bg_status bg_submit(bg_ctx_t ctx, const bg_request* req, uint64_t* ticket);
 
 /* Never blocks. BG_PENDING while the ticket runs; otherwise BG_OK with *out
