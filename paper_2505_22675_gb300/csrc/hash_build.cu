@@ -9,7 +9,10 @@
 //   K4 sat           : summed-area table of the counts (2-D prefix sums), so a
 //                      rectangle of cells is counted with four loads
 //
-// All four passes stream through HBM; none has a data-dependent loop.
+// All four passes stream through HBM; none has a data-dependent loop. An input
+// of at most 65,536 soundings over at most 12,000 cells (a serving tile) takes
+// them in one 1024-thread block instead (k_hash_small), with its counts in
+// shared memory: one launch instead of eight.
 #include <algorithm>
 #include <climits>
 #include <cmath>
@@ -268,6 +271,93 @@ __global__ void k_sat_apply(const int* __restrict__ cs, const int* __restrict__ 
     }
 }
 
+// ------------------------------------------------------- small inputs, one block
+// A tile of a few tens of thousands of soundings spends its build on eight
+// launches of tiny kernels. One 1024-thread block does the same passes with
+// the counts in shared memory: (pack,) count, exclusive scan, summed-area
+// table, scatter. cell_start and the table are those of the multi-kernel
+// passes; the order of records within a cell comes from shared-memory
+// atomics instead of global ones (every search result is keyed by (d2,
+// index), so no result depends on it).
+constexpr int kSmallThreads = 1024;
+constexpr int64_t kSmallN = 1 << 16;
+constexpr int64_t kSmallCells = 12000;  // counts + scan sums within 48 KB
+
+// Exclusive scan over the 1024 threads of a block; ws holds 33 ints, ws[32]
+// the total on return.
+__device__ __forceinline__ int block_excl_scan_1024(int v, int* ws) {
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    const int inc = warp_incl_scan(v);
+    if (l == 31) ws[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        const int s = ws[l];
+        const int si = warp_incl_scan(s);
+        ws[l] = si - s;
+        if (l == 31) ws[32] = si;
+    }
+    __syncthreads();
+    return ws[w] + inc - v;
+}
+
+// pack: also write the upload-order records (when no earlier pass did).
+// Dynamic shared memory: (ncx * ncy + 34) ints.
+__global__ void __launch_bounds__(kSmallThreads) k_hash_small(
+    const int32_t* __restrict__ x, const int32_t* __restrict__ y, const float* __restrict__ z,
+    int n, int pack, int4* __restrict__ orig, CellGeom g, int* __restrict__ cell_start,
+    int4* __restrict__ rec, int* __restrict__ sat) {
+    extern __shared__ int cnt[];  // ncells counts, then starts, then cursors; + total + 33
+    const int ncells = g.ncx * g.ncy;
+    int* ws = cnt + ncells + 1;
+    for (int c = threadIdx.x; c < ncells; c += blockDim.x) cnt[c] = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int xi = x[i], yi = y[i];
+        const float zi = z[i];
+        const int valid = isnan(zi) ? 0 : 1;
+        if (pack) orig[i] = make_int4(xi, yi, __float_as_int(zi), valid);
+        if (valid) atomicAdd(&cnt[cell_index(g, xi, yi)], 1);
+    }
+    __syncthreads();
+    // exclusive scan, thread t over the cells [t * per, (t + 1) * per)
+    const int per = (ncells + kSmallThreads - 1) / kSmallThreads;
+    const int c0 = min(ncells, (int)threadIdx.x * per), c1 = min(ncells, c0 + per);
+    int s = 0;
+    for (int c = c0; c < c1; ++c) s += cnt[c];
+    int run = block_excl_scan_1024(s, ws);
+    for (int c = c0; c < c1; ++c) {
+        const int v = cnt[c];
+        cnt[c] = run;
+        cell_start[c] = run;
+        run += v;
+    }
+    if (threadIdx.x == 0) {
+        cnt[ncells] = ws[32];
+        cell_start[ncells] = ws[32];
+    }
+    __syncthreads();
+    // summed-area table: column xx walks the rows; the row prefix of row yy
+    // at column xx is start[yy * ncx + xx] - start[yy * ncx]
+    const int64_t W = g.ncx + 1;
+    for (int xx = threadIdx.x; xx < W; xx += blockDim.x) {
+        int col = 0;
+        sat[xx] = 0;
+        for (int yy = 0; yy < g.ncy; ++yy) {
+            col += cnt[yy * g.ncx + xx] - cnt[yy * g.ncx];
+            sat[(int64_t)(yy + 1) * W + xx] = col;
+        }
+    }
+    __syncthreads();  // the starts become the scatter's cursors
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const float zi = z[i];
+        if (!isnan(zi)) {
+            const int xi = x[i], yi = y[i];
+            const int pos = atomicAdd(&cnt[cell_index(g, xi, yi)], 1);
+            rec[pos] = make_int4(xi, yi, __float_as_int(zi), i);
+        }
+    }
+}
+
 int grid_for(int64_t n, int per_block, int cap) {
     int64_t b = (n + per_block - 1) / per_block;
     if (b < 1) b = 1;
@@ -293,6 +383,35 @@ struct Scratch {
         if (p) dfree(ctx, p, bytes, st);
     }
 };
+}  // namespace
+
+namespace {
+// The cell side for a bounding box a = (x0, y0, x1, y1) holding nvalid soundings:
+// the caller's hint, else about four soundings per cell at the mean density of
+// the box (measured on the swath: 2 or 8 per cell make the k-NN 3-6% slower),
+// widened until the tables fit.
+int64_t pick_cell_side(const int32_t* a, int64_t nvalid, int32_t cell_hint) {
+    const int64_t W = (int64_t)a[2] - a[0] + 1, H = (int64_t)a[3] - a[1] + 1;
+    int64_t cs = cell_hint;
+    if (cs <= 0) {
+        const double rho = (double)nvalid / ((double)W * (double)H);
+        cs = (int64_t)std::ceil(std::sqrt(4.0 / rho));
+    }
+    if (cs < 1) cs = 1;
+    if (cs > kCoordLimit) cs = kCoordLimit;
+    const int64_t max_cells = std::min<int64_t>((int64_t)1 << 28, 16 * nvalid + 4096);
+    for (;;) {
+        const int64_t ncx = (W + cs - 1) / cs, ncy = (H + cs - 1) / cs;
+        if (ncx * ncy <= max_cells && (ncx + 1) * (ncy + 1) < ((int64_t)1 << 31)) break;
+        cs = cs + cs / 4 + 1;
+    }
+    return cs;
+}
+
+int64_t cells_of(const int32_t* a, int64_t cs) {
+    const int64_t W = (int64_t)a[2] - a[0] + 1, H = (int64_t)a[3] - a[1] + 1;
+    return ((W + cs - 1) / cs) * ((H + cs - 1) / cs);
+}
 }  // namespace
 
 bg_status build_soundings(bg_ctx_s* ctx, const int32_t* x, const int32_t* y, const float* z,
@@ -327,16 +446,26 @@ bg_status build_soundings(bg_ctx_s* ctx, const int32_t* x, const int32_t* y, con
         s->bytes += (size_t)n * 16;
         s->h.orig = (const int4*)s->d_orig;
     }
-    if ((rc = accbuf.alloc(8 * sizeof(int))) != BG_OK) return rc;
-    int* acc = (int*)accbuf.p;  // min x, min y, max x, max y, valid count, out-of-range count
-    k_bbox_init<<<1, 32, 0, st>>>(acc);
-    note_launches(1);
-    if (n > 0) {
-        k_validate_pack<<<grid_for(n, kThreads * 4, 152 * 16), kThreads, 0, st>>>(
-            dx, dy, dz, n, (int4*)s->d_orig, acc);
-        note_launches(1);
+    // a small input whose bounding box the caller scanned on the host is packed
+    // by the one-block build itself
+    bool pack_small = false;
+    if (known && n > 0 && n <= kSmallN && known->n_valid > 0 && known->out_of_range == 0) {
+        const int32_t kb[4] = {known->x0, known->y0, known->x1, known->y1};
+        pack_small = cells_of(kb, pick_cell_side(kb, known->n_valid, cell_hint)) <= kSmallCells;
     }
-    BG_CUDA(cudaGetLastError());
+    int* acc = nullptr;
+    if (!pack_small) {
+        if ((rc = accbuf.alloc(8 * sizeof(int))) != BG_OK) return rc;
+        acc = (int*)accbuf.p;  // min x, min y, max x, max y, valid count, out-of-range count
+        k_bbox_init<<<1, 32, 0, st>>>(acc);
+        note_launches(1);
+        if (n > 0) {
+            k_validate_pack<<<grid_for(n, kThreads * 4, 152 * 16), kThreads, 0, st>>>(
+                dx, dy, dz, n, (int4*)s->d_orig, acc);
+            note_launches(1);
+        }
+        BG_CUDA(cudaGetLastError());
+    }
     int32_t a[6];
     if (known) {
         // the caller scanned the (host) input already: no device round trip
@@ -362,21 +491,7 @@ bg_status build_soundings(bg_ctx_s* ctx, const int32_t* x, const int32_t* y, con
     if (nvalid == 0) return BG_OK;  // every interpolation over this handle yields NaN
 
     const int64_t W = (int64_t)a[2] - a[0] + 1, H = (int64_t)a[3] - a[1] + 1;
-    int64_t cs = cell_hint;
-    if (cs <= 0) {
-        // about four soundings per cell at the mean density of the bounding box
-        // (measured on the swath: 2 or 8 per cell make the k-NN 3-6% slower)
-        const double rho = (double)nvalid / ((double)W * (double)H);
-        cs = (int64_t)std::ceil(std::sqrt(4.0 / rho));
-    }
-    if (cs < 1) cs = 1;
-    if (cs > kCoordLimit) cs = kCoordLimit;
-    const int64_t max_cells = std::min<int64_t>((int64_t)1 << 28, 16 * nvalid + 4096);
-    for (;;) {
-        const int64_t ncx = (W + cs - 1) / cs, ncy = (H + cs - 1) / cs;
-        if (ncx * ncy <= max_cells && (ncx + 1) * (ncy + 1) < ((int64_t)1 << 31)) break;
-        cs = cs + cs / 4 + 1;
-    }
+    const int64_t cs = pick_cell_side(a, nvalid, cell_hint);
     const int32_t ncx = (int32_t)((W + cs - 1) / cs), ncy = (int32_t)((H + cs - 1) / cs);
     const int64_t ncells = (int64_t)ncx * ncy;
     s->info.bbox_x0_cm = a[0];
@@ -397,34 +512,42 @@ bg_status build_soundings(bg_ctx_s* ctx, const int32_t* x, const int32_t* y, con
     if ((rc = dalloc(ctx, &s->d_rec, rec_bytes, st)) != BG_OK) return rc;
     s->bytes += rec_bytes;
 
-    const int nb = (int)((ncells + kScanTile - 1) / kScanTile);
-    // chunks of rows for the column prefix of the SAT (grid.y stays <= 65535)
-    const int sat_rows = std::max(kSatRows, (ncy + 65534) / 65535);
-    const int nch = (ncy + sat_rows - 1) / sat_rows;
-    const size_t count_bytes = (size_t)ncells * 4;
-    const size_t bsum_bytes = (size_t)(nb + 1) * 4;
-    const size_t csum_bytes = (size_t)nch * (ncx + 1) * 4;
-    if ((rc = scratch.alloc(count_bytes + bsum_bytes + csum_bytes + 64)) != BG_OK) return rc;
-    int* count = (int*)scratch.p;
-    int* bsum = count + ncells;
-    int* csum = bsum + nb + 1;
-    int* cell_start = (int*)s->d_cell_start;
-
     const CellGeom g{a[0], a[1], (int32_t)cs, ncx, ncy};
-    BG_CUDA(cudaMemsetAsync(count, 0, count_bytes, st));
-    k_cell_hist<<<grid_for(n, kThreads * 4, 152 * 16), kThreads, 0, st>>>(
-        (const int4*)s->d_orig, n, g, count);
-    k_scan_reduce<<<nb, kThreads, 0, st>>>(count, ncells, bsum);
-    k_scan_blocksums<<<1, kThreads, 0, st>>>(bsum, nb, cell_start + ncells);
-    k_scan_apply<<<nb, kThreads, 0, st>>>(count, ncells, bsum, cell_start, count);
-    k_scatter<<<grid_for(n, kThreads * 4, 152 * 16), kThreads, 0, st>>>(
-        (const int4*)s->d_orig, n, g, count, (int4*)s->d_rec);
-    const dim3 sg((ncx + 1 + 255) / 256, nch);
-    k_sat_chunk<<<sg, 256, 0, st>>>(cell_start, ncx, ncy, sat_rows, csum);
-    k_sat_chunkscan<<<(ncx + 1 + 255) / 256, 256, 0, st>>>(csum, ncx, nch);
-    k_sat_apply<<<sg, 256, 0, st>>>(cell_start, csum, ncx, ncy, sat_rows, (int*)s->d_sat);
-    note_launches(8);
-    BG_CUDA(cudaGetLastError());
+    int* cell_start = (int*)s->d_cell_start;
+    if (n <= kSmallN && ncells <= kSmallCells) {
+        k_hash_small<<<1, kSmallThreads, (size_t)(ncells + 34) * sizeof(int), st>>>(
+            dx, dy, dz, (int)n, pack_small ? 1 : 0, (int4*)s->d_orig, g, cell_start,
+            (int4*)s->d_rec, (int*)s->d_sat);
+        note_launches(1);
+        BG_CUDA(cudaGetLastError());
+    } else {
+        const int nb = (int)((ncells + kScanTile - 1) / kScanTile);
+        // chunks of rows for the column prefix of the SAT (grid.y stays <= 65535)
+        const int sat_rows = std::max(kSatRows, (ncy + 65534) / 65535);
+        const int nch = (ncy + sat_rows - 1) / sat_rows;
+        const size_t count_bytes = (size_t)ncells * 4;
+        const size_t bsum_bytes = (size_t)(nb + 1) * 4;
+        const size_t csum_bytes = (size_t)nch * (ncx + 1) * 4;
+        if ((rc = scratch.alloc(count_bytes + bsum_bytes + csum_bytes + 64)) != BG_OK) return rc;
+        int* count = (int*)scratch.p;
+        int* bsum = count + ncells;
+        int* csum = bsum + nb + 1;
+
+        BG_CUDA(cudaMemsetAsync(count, 0, count_bytes, st));
+        k_cell_hist<<<grid_for(n, kThreads * 4, 152 * 16), kThreads, 0, st>>>(
+            (const int4*)s->d_orig, n, g, count);
+        k_scan_reduce<<<nb, kThreads, 0, st>>>(count, ncells, bsum);
+        k_scan_blocksums<<<1, kThreads, 0, st>>>(bsum, nb, cell_start + ncells);
+        k_scan_apply<<<nb, kThreads, 0, st>>>(count, ncells, bsum, cell_start, count);
+        k_scatter<<<grid_for(n, kThreads * 4, 152 * 16), kThreads, 0, st>>>(
+            (const int4*)s->d_orig, n, g, count, (int4*)s->d_rec);
+        const dim3 sg((ncx + 1 + 255) / 256, nch);
+        k_sat_chunk<<<sg, 256, 0, st>>>(cell_start, ncx, ncy, sat_rows, csum);
+        k_sat_chunkscan<<<(ncx + 1 + 255) / 256, 256, 0, st>>>(csum, ncx, nch);
+        k_sat_apply<<<sg, 256, 0, st>>>(cell_start, csum, ncx, ncy, sat_rows, (int*)s->d_sat);
+        note_launches(8);
+        BG_CUDA(cudaGetLastError());
+    }
 
     s->h.rec = (const int4*)s->d_rec;
     s->h.cell_start = cell_start;
