@@ -82,6 +82,39 @@ def test_mix_alone_and_direct_are_bitwise_equal():
         bg.ctx_destroy(ctx)
 
 
+def test_large_grids_copied_out_in_shares_are_bitwise_equal():
+    """Grids of 256 KB and more leave pinned staging in four shares (the
+    completion thread and three helpers): 301 x 301 and 517 x 517 nodes (odd
+    sizes, so the last share takes a remainder), IDW and kriging, submitted
+    one at a time and then all at once, against the direct API."""
+    import torch
+
+    import paper_2505_22675_gb300 as bg
+    tiles = [(synth.tile(seed=31, n=20_000, side_cm=60_200, cell_cm=200), 0),
+             (synth.tile(seed=32, n=30_000, side_cm=60_200, cell_cm=200), 1),
+             (synth.tile(seed=33, n=40_000, side_cm=103_400, cell_cm=200), 1),
+             (synth.tile(seed=34, n=25_000, side_cm=103_400, cell_cm=200), 0)]
+    assert all(w.grid.m * 4 >= 256 << 10 for w, _ in tiles)
+    ctx = bg.ctx_create(0)
+    try:
+        alone = []
+        for w, m in tiles:
+            t, d, v = _submit(bg, ctx, w, m)
+            assert bg.wait(ctx, t, 60_000).status == 0
+            alone.append((d, v))
+        mix = [_submit(bg, ctx, w, m) for w, m in tiles]
+        for (t, d, v), (ad, av), (w, m) in zip(mix, alone, tiles):
+            assert bg.wait(ctx, t, 60_000).status == 0
+            dd, dv = _direct(bg, torch, ctx, w, m)
+            for got in (d, ad):
+                assert np.array_equal(got.view(np.uint32), dd.view(np.uint32))
+            if m == 1:
+                for got in (v, av):
+                    assert np.array_equal(got.view(np.uint32), dv.view(np.uint32))
+    finally:
+        bg.ctx_destroy(ctx)
+
+
 def test_served_results_match_the_oracle():
     import paper_2505_22675_gb300 as bg
     tiles = [t for t in _tiles(10, seed=5, scale=0.01)][:6]
