@@ -7,21 +7,21 @@
 namespace bg {
 namespace {
 
-// Packed pass: one (16 * kStrip) x 8 node patch per block, a strip of kStrip
-// nodes per thread.
-template <int K>
+// Packed pass: one (16 * kLen) x 8 node patch per block, a strip of kLen
+// nodes per thread (strip_len_for).
+template <int K, int kLen>
 __global__ void __launch_bounds__(128) k_idw(HashView h, GridView g, int k, float power,
                                              float* __restrict__ depth,
                                              int32_t* __restrict__ nbr, int* __restrict__ flag) {
     __shared__ uint64_t heap[K * 128];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int gx = (g.nx + 16 * kStrip - 1) / (16 * kStrip);
-    const NodeIdx o = strip_origin(blockIdx.x % gx, blockIdx.x / gx, warp, lane);
+    const int gx = (g.nx + 16 * kLen - 1) / (16 * kLen);
+    const NodeIdx o = strip_origin<kLen>(blockIdx.x % gx, blockIdx.x / gx, warp, lane);
     if (o.j >= g.ny) return;
     uint64_t* hp = heap + threadIdx.x;
     const int64_t row = (int64_t)o.j * g.nx;
     if (h.n_valid == 0) {
-        for (int i = o.i; i < min(o.i + kStrip, g.nx); ++i) {
+        for (int i = o.i; i < min(o.i + kLen, g.nx); ++i) {
             depth[row + i] = __int_as_float(0x7fc00000);
             if (nbr)
                 for (int q = 0; q < k; ++q) nbr[(row + i) * k + q] = -1;
@@ -30,7 +30,7 @@ __global__ void __launch_bounds__(128) k_idw(HashView h, GridView g, int k, floa
     }
     const int bits = h.idx_bits;
     const uint64_t mask = (1ull << bits) - 1;
-    knn_strip<128>(h, g, K, o.i, o.j, hp, flag, [&](int i, int cnt) {
+    auto emit = [&](int i, int cnt) {
         const int keff = min(cnt, k);
         depth[row + i] = idw_from(h, keff, power, [&](int q, uint64_t& dd, int& ii) {
             const uint64_t key = hp[q * 128];
@@ -38,7 +38,8 @@ __global__ void __launch_bounds__(128) k_idw(HashView h, GridView g, int k, floa
             ii = (int)(key & mask);
         });
         if (nbr) emit_ids<128>(nbr + (row + i) * k, hp, k, keff, mask);
-    });
+    };
+    knn_strip<128, decltype(emit), true, kLen>(h, g, K, o.i, o.j, hp, flag, emit);
 }
 
 // Wide-key pass over the nodes the packed pass could not take; it returns at
@@ -60,11 +61,17 @@ template <int K>
 bg_status launch_k(const HashView& h, const GridView& g, int k, float power, float* depth,
                    int32_t* nbr, int* d_flag, cudaStream_t st, bg_ctx_s* prof_ctx) {
     const int64_t nb = (int64_t)((g.nx + 15) / 16) * ((g.ny + 7) / 8);
-    const int64_t nbs = (int64_t)((g.nx + 16 * kStrip - 1) / (16 * kStrip)) * ((g.ny + 7) / 8);
+    const int len = strip_len_for((int64_t)g.nx * g.ny);
+    const int64_t nbs = (int64_t)((g.nx + 16 * len - 1) / (16 * len)) * ((g.ny + 7) / 8);
     BG_CUDA(cudaMemsetAsync(d_flag, 0, sizeof(int), st));
     {
         ProfScope ps(prof_ctx, kProfIdw, (int64_t)g.nx * g.ny, st);
-        k_idw<K><<<(unsigned)nbs, 128, 0, st>>>(h, g, k, power, depth, nbr, d_flag);
+        if (len == 1)
+            k_idw<K, 1><<<(unsigned)nbs, 128, 0, st>>>(h, g, k, power, depth, nbr, d_flag);
+        else if (len == 2)
+            k_idw<K, 2><<<(unsigned)nbs, 128, 0, st>>>(h, g, k, power, depth, nbr, d_flag);
+        else
+            k_idw<K, 4><<<(unsigned)nbs, 128, 0, st>>>(h, g, k, power, depth, nbr, d_flag);
     }
     k_idw_wide<K><<<(unsigned)std::min<int64_t>(nb, 152 * 4), 128, 0, st>>>(h, g, k, power, depth,
                                                                         nbr, d_flag);

@@ -8,23 +8,24 @@
 namespace bg {
 namespace {
 
-// grid rows [j0, j1); j0 is a multiple of 8; a strip of kStrip nodes per thread.
-// 64-thread blocks: the 16 KB heap (K = 32) plus the per-block reserve lets
-// 13 blocks (26 warps) share an SM, against 6 blocks (24 warps) of 128.
-template <int K>
+// grid rows [j0, j1); j0 is a multiple of 8; a strip of kLen nodes per thread
+// (strip_len_for). 64-thread blocks: the 16 KB heap (K = 32) plus the
+// per-block reserve lets 13 blocks (26 warps) share an SM, against 6 blocks
+// (24 warps) of 128.
+template <int K, int kLen>
 __global__ void __launch_bounds__(64) k_knn_ids(HashView h, GridView g, int k, int j0, int j1,
                                                 int32_t* __restrict__ ids, int* __restrict__ flag) {
     __shared__ uint64_t heap[K * 64];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int gx = (g.nx + 16 * kStrip - 1) / (16 * kStrip);
-    // (16 * kStrip) x 4 node patches: warp w covers columns w * 8 * kStrip ..
+    const int gx = (g.nx + 16 * kLen - 1) / (16 * kLen);
+    // (16 * kLen) x 4 node patches: warp w covers columns w * 8 * kLen ..
     const int px = blockIdx.x % gx, py = j0 / 4 + blockIdx.x / gx;
-    const NodeIdx o{px * 16 * kStrip + warp * 8 * kStrip + (lane & 7) * kStrip, py * 4 + (lane >> 3)};
+    const NodeIdx o{px * 16 * kLen + warp * 8 * kLen + (lane & 7) * kLen, py * 4 + (lane >> 3)};
     if (o.j >= j1) return;
     uint64_t* hp = heap + threadIdx.x;
     int32_t* base = ids + ((int64_t)(o.j - j0) * g.nx) * k;
     if (h.n_valid == 0) {
-        for (int i = o.i; i < min(o.i + kStrip, g.nx); ++i)
+        for (int i = o.i; i < min(o.i + kLen, g.nx); ++i)
             for (int q = 0; q < k; ++q) base[(int64_t)i * k + q] = -1;
         return;
     }
@@ -46,7 +47,7 @@ __global__ void __launch_bounds__(64) k_knn_ids(HashView h, GridView g, int k, i
         }
         emit_ids<64>(out, hp, k, cnt, mask);
     };
-    knn_strip<64, decltype(emit), false>(h, g, K, o.i, o.j, hp, flag, emit);
+    knn_strip<64, decltype(emit), false, kLen>(h, g, K, o.i, o.j, hp, flag, emit);
 }
 
 template <int K>
@@ -126,7 +127,8 @@ bg_status launch_k(const HashView& h, const GridView& g, int k, const OkParams& 
     for (int64_t j0 = 0; j0 < g.ny; j0 += rows) {
         const int64_t j1 = std::min<int64_t>(g.ny, j0 + rows);
         const int64_t nb = (int64_t)gx * ((j1 - j0 + 7) / 8);
-        const int64_t nbs = (int64_t)((g.nx + 16 * kStrip - 1) / (16 * kStrip)) * ((j1 - j0 + 3) / 4);
+        const int len = strip_len_for((j1 - j0) * (int64_t)g.nx);
+        const int64_t nbs = (int64_t)((g.nx + 16 * len - 1) / (16 * len)) * ((j1 - j0 + 3) / 4);
         int32_t* chunk_ids = nbr ? nbr + j0 * g.nx * k : (int32_t*)((char*)scratch + flag_bytes);
         cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), st);
         if (e != cudaSuccess) {
@@ -136,7 +138,12 @@ bg_status launch_k(const HashView& h, const GridView& g, int k, const OkParams& 
         const int64_t nodes = (j1 - j0) * g.nx;
         {
             ProfScope ps(ctx, kProfKnnIds, nodes, st);
-            k_knn_ids<K><<<(unsigned)nbs, 64, 0, st>>>(h, g, k, (int)j0, (int)j1, chunk_ids, flag);
+            if (len == 1)
+                k_knn_ids<K, 1><<<(unsigned)nbs, 64, 0, st>>>(h, g, k, (int)j0, (int)j1, chunk_ids, flag);
+            else if (len == 2)
+                k_knn_ids<K, 2><<<(unsigned)nbs, 64, 0, st>>>(h, g, k, (int)j0, (int)j1, chunk_ids, flag);
+            else
+                k_knn_ids<K, 4><<<(unsigned)nbs, 64, 0, st>>>(h, g, k, (int)j0, (int)j1, chunk_ids, flag);
         }
         k_knn_ids_wide<K><<<(unsigned)std::min<int64_t>(nb, 152 * 4), 128, 0, st>>>(
             h, g, k, (int)j0, (int)j1, chunk_ids, flag);
