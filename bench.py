@@ -908,25 +908,53 @@ def bench_ours(args):
     xh, yh, zh = (torch.from_numpy(a).pin_memory() for a in (w.x_cm, w.y_cm, w.z_m))
     out_h = [torch.empty(m, pin_memory=True) for _ in range(3)]
 
-    def e2e_step():
-        # the grids go to pinned host memory chunk by chunk, each chunk's copy
-        # overlapping the later chunks' kernels (bg_interp_idw_okrige_host)
-        s = bg.soundings_upload(ctx, xh, yh, zh, stream=stream)
-        bg.interp_idw_okrige_host(s, grid, IDW_K, IDW_P, OK_K, vgm, d_idw, d_ok, v_ok, *out_h)
-        bg.soundings_destroy(s)
+    # Two steps in flight, as a survey pipeline streams swaths: steps alternate
+    # between two streams with their own device and pinned host buffers, so a
+    # step's upload overlaps the previous step's kernels. Each step uploads its
+    # soundings from pinned host memory and gets its three grids back in pinned
+    # host memory (bg_interp_idw_okrige_host copies each row chunk's grids while
+    # the later chunks compute); a step's handle is destroyed, and its buffers
+    # reused, only after its stream is synchronized two steps later.
+    e_streams = [stream, torch.cuda.Stream(dev)]
+    e_dev = [(d_idw, d_ok, v_ok), tuple(torch.empty(m, device=dev) for _ in range(3))]
+    e_host = [out_h, [torch.empty(m, pin_memory=True) for _ in range(3)]]
+    live = [None, None]
 
-    e2e_step()
-    torch.cuda.synchronize()
+    def e2e_step(i):
+        j = i % 2
+        st = e_streams[j]
+        if live[j] is not None:
+            st.synchronize()
+            bg.soundings_destroy(live[j])
+            live[j] = None
+        with torch.cuda.stream(st):
+            s = bg.soundings_upload(ctx, xh, yh, zh, stream=st)
+            bg.interp_idw_okrige_host(s, grid, IDW_K, IDW_P, OK_K, vgm, *e_dev[j], *e_host[j],
+                                      stream=st)
+        live[j] = s
+
+    def e2e_drain():
+        for j in (0, 1):
+            e_streams[j].synchronize()
+            if live[j] is not None:
+                bg.soundings_destroy(live[j])
+                live[j] = None
+
+    e2e_step(0)
+    e2e_step(1)
+    e2e_drain()
     barrier()
-    e_steps = max(1, args.steps)
+    e_steps = max(2, args.steps)
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
-    t0.record(stream)
-    for _ in range(e_steps):
-        e2e_step()
-    t1.record(stream)
-    torch.cuda.synchronize()
+    t0.record(e_streams[0])
+    for i in range(e_steps):
+        e2e_step(i)
+    e_streams[0].wait_stream(e_streams[1])
+    t1.record(e_streams[0])
+    t1.synchronize()
     e2e_ms = t0.elapsed_time(t1) / e_steps
+    e2e_drain()
     if ws > 1:
         import torch.distributed as dist
         t = torch.tensor([e2e_ms], device=dev)
@@ -1012,7 +1040,8 @@ def bench_ours(args):
             "errors_vs_oracle": errors,
             "e2e": {"value": ws * m / (e2e_ms / 1e3), "unit": "nodes/s",
                     "h2d_bytes_per_step": int(12 * w.x_cm.size),
-                    "d2h_bytes_per_step": int(12 * m), "ms_per_step": e2e_ms, "steps": e_steps},
+                    "d2h_bytes_per_step": int(12 * m), "ms_per_step": e2e_ms, "steps": e_steps,
+                    "in_flight": 2},
             "gpu_launches": int(launches), "clocks": clocks, "nan_outputs": bad,
         }
         if slab is not None:
