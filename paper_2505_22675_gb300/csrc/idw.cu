@@ -80,13 +80,13 @@ bg_status launch_k(const HashView& h, const GridView& g, int k, float power, flo
     return BG_OK;
 }
 
-// Query points: kStrip consecutive points per thread (knn_chain).
-template <int K>
+// Query points: kLen consecutive points per thread (knn_chain).
+template <int K, int kLen>
 __global__ void __launch_bounds__(128) k_idw_pts(HashView h, PointsView q, int k, float power,
                                                  float* __restrict__ depth,
                                                  int32_t* __restrict__ nbr, int* __restrict__ flag) {
     __shared__ uint64_t heap[K * 128];
-    const int64_t p0 = ((int64_t)blockIdx.x * 128 + threadIdx.x) * kStrip;
+    const int64_t p0 = ((int64_t)blockIdx.x * 128 + threadIdx.x) * kLen;
     if (p0 >= q.m) return;
     uint64_t* hp = heap + threadIdx.x;
     const int bits = h.idx_bits;
@@ -97,10 +97,10 @@ __global__ void __launch_bounds__(128) k_idw_pts(HashView h, PointsView q, int k
             for (int i = 0; i < k; ++i) nbr[p * k + i] = -1;
     };
     if (h.n_valid == 0) {
-        for (int64_t p = p0; p < min(p0 + kStrip, q.m); ++p) none(p);
+        for (int64_t p = p0; p < min(p0 + kLen, q.m); ++p) none(p);
         return;
     }
-    knn_chain<128>(h, q.x, q.y, p0, q.m, K, hp, flag, [&](int64_t p, int cnt) {
+    auto emit = [&](int64_t p, int cnt) {
         if (cnt < 0) {
             none(p);
             return;
@@ -112,7 +112,8 @@ __global__ void __launch_bounds__(128) k_idw_pts(HashView h, PointsView q, int k
             ii = (int)(key & mask);
         });
         if (nbr) emit_ids<128>(nbr + p * k, hp, k, keff, mask);
-    });
+    };
+    knn_chain<128, decltype(emit), kLen>(h, q.x, q.y, p0, q.m, K, hp, flag, emit);
 }
 
 template <int K>
@@ -130,12 +131,18 @@ __global__ void __launch_bounds__(128) k_idw_pts_wide(HashView h, PointsView q, 
 template <int K>
 bg_status launch_pts_k(const HashView& h, const PointsView& q, int k, float power, float* depth,
                        int32_t* nbr, int* d_flag, cudaStream_t st, bg_ctx_s* prof_ctx) {
-    const int64_t threads = (q.m + kStrip - 1) / kStrip;
+    const int len = strip_len_for(q.m);
+    const int64_t threads = (q.m + len - 1) / len;
     const int64_t nb = (threads + 127) / 128;
     BG_CUDA(cudaMemsetAsync(d_flag, 0, sizeof(int), st));
     {
         ProfScope ps(prof_ctx, kProfIdw, q.m, st);
-        k_idw_pts<K><<<(unsigned)nb, 128, 0, st>>>(h, q, k, power, depth, nbr, d_flag);
+        if (len == 1)
+            k_idw_pts<K, 1><<<(unsigned)nb, 128, 0, st>>>(h, q, k, power, depth, nbr, d_flag);
+        else if (len == 2)
+            k_idw_pts<K, 2><<<(unsigned)nb, 128, 0, st>>>(h, q, k, power, depth, nbr, d_flag);
+        else
+            k_idw_pts<K, 4><<<(unsigned)nb, 128, 0, st>>>(h, q, k, power, depth, nbr, d_flag);
     }
     k_idw_pts_wide<K><<<(unsigned)std::min<int64_t>((q.m + 127) / 128, 152 * 4), 128, 0, st>>>(
         h, q, k, power, depth, nbr, d_flag);

@@ -513,8 +513,8 @@ __device__ __forceinline__ void knn_strip(const HashView& h, const GridView& g, 
 }
 
 // ---------------------------------------------------------------------------
-// Query points instead of grid nodes. A thread takes kStrip consecutive points
-// of the caller's list. The next point's K-th distance is at most the previous
+// Query points instead of grid nodes. A thread takes kLen consecutive points
+// of the caller's list (strip_len_for the list's length). The next point's K-th distance is at most the previous
 // point's plus the distance between the two (triangle inequality); that bound
 // is used when the step is no longer than the previous K-th distance (lists
 // in scan order, such as the holes of a grid), else the summed-area table's.
@@ -525,17 +525,17 @@ __device__ __forceinline__ bool query_in_range(int qx, int qy) {
     return qx > -kQueryLimit && qx < kQueryLimit && qy > -kQueryLimit && qy < kQueryLimit;
 }
 
-// Packed-key k-NN of points p0 .. p0 + kStrip - 1 (those below m). emit(p, cnt)
+// Packed-key k-NN of points p0 .. p0 + kLen - 1 (those below m). emit(p, cnt)
 // runs after each point with its keys sorted ascending in hp[0 .. cnt), or
 // with cnt = -1 for a point outside the coordinate range; a point whose table
 // bound does not fit the packed key is left to the wide pass (*flag = 1).
-template <int S, class Emit>
+template <int S, class Emit, int kLen = kStrip>
 __device__ __forceinline__ void knn_chain(const HashView& h, const int32_t* __restrict__ px,
                                           const int32_t* __restrict__ py, int64_t p0, int64_t m,
                                           int kc, uint64_t* hp, int* flag, Emit emit) {
     int64_t prev = -1;  // K-th squared distance of the previous point, -1 if none
     int qxp = 0, qyp = 0;
-    for (int s = 0; s < kStrip; ++s) {
+    for (int s = 0; s < kLen; ++s) {
         const int64_t p = p0 + s;
         if (p >= m) break;
         const int qx = __ldg(px + p), qy = __ldg(py + p);

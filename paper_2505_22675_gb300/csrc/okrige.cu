@@ -184,24 +184,23 @@ bg_status launch_k(const HashView& h, const GridView& g, int k, const OkParams& 
 
 // ------------------------------------------------------------ query points
 
-// points [p0, p1), kStrip consecutive points per thread
-template <int K>
+// points [p0, p1), kLen consecutive points per thread (strip_len_for)
+template <int K, int kLen>
 __global__ void __launch_bounds__(128) k_knn_ids_pts(HashView h, PointsView q, int k, int64_t p0,
                                                      int64_t p1, int32_t* __restrict__ ids,
                                                      int* __restrict__ flag) {
     __shared__ uint64_t heap[K * 128];
-    const int64_t a = p0 + ((int64_t)blockIdx.x * 128 + threadIdx.x) * kStrip;
+    const int64_t a = p0 + ((int64_t)blockIdx.x * 128 + threadIdx.x) * kLen;
     if (a >= p1) return;
     uint64_t* hp = heap + threadIdx.x;
     if (h.n_valid == 0) {
-        for (int64_t p = a; p < min(a + kStrip, p1); ++p)
+        for (int64_t p = a; p < min(a + kLen, p1); ++p)
             for (int i = 0; i < k; ++i) ids[(p - p0) * k + i] = -1;
         return;
     }
     const uint64_t mask = (1ull << h.idx_bits) - 1;
-    knn_chain<128>(h, q.x, q.y, a, p1, K, hp, flag, [&](int64_t p, int cnt) {
-        emit_ids<128>(ids + (p - p0) * k, hp, k, cnt, mask);
-    });
+    auto emit = [&](int64_t p, int cnt) { emit_ids<128>(ids + (p - p0) * k, hp, k, cnt, mask); };
+    knn_chain<128, decltype(emit), kLen>(h, q.x, q.y, a, p1, K, hp, flag, emit);
 }
 
 template <int K>
@@ -258,10 +257,16 @@ bg_status launch_pts_k(const HashView& h, const PointsView& q, int k, const OkPa
             rc = cuda_fail(e, "memset");
             break;
         }
-        const int64_t nb = ((n + kStrip - 1) / kStrip + 127) / 128;
+        const int len = strip_len_for(n);
+        const int64_t nb = ((n + len - 1) / len + 127) / 128;
         {
             ProfScope ps(ctx, kProfKnnIds, n, st);
-            k_knn_ids_pts<K><<<(unsigned)nb, 128, 0, st>>>(h, q, k, p0, p1, chunk_ids, flag);
+            if (len == 1)
+                k_knn_ids_pts<K, 1><<<(unsigned)nb, 128, 0, st>>>(h, q, k, p0, p1, chunk_ids, flag);
+            else if (len == 2)
+                k_knn_ids_pts<K, 2><<<(unsigned)nb, 128, 0, st>>>(h, q, k, p0, p1, chunk_ids, flag);
+            else
+                k_knn_ids_pts<K, 4><<<(unsigned)nb, 128, 0, st>>>(h, q, k, p0, p1, chunk_ids, flag);
         }
         k_knn_ids_pts_wide<K><<<(unsigned)std::min<int64_t>((n + 127) / 128, 152 * 4), 128, 0, st>>>(
             h, q, k, p0, p1, chunk_ids, flag);
